@@ -1,0 +1,458 @@
+/*
+ * lbmhd_oracle.c -- plain, slow, FP64 CPU oracle for the filtered lattice
+ * Boltzmann MHD time step of Flint & Vahala, "Lattice Boltzmann Large Eddy
+ * Simulation Model of MHD" (arXiv:1607.08675).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA path is checked against.  Only the test suite, the package smoke check
+ * and the CPU-baseline leg of the benchmark may build, load or call it.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Written for readability, not speed: scalar loops, IEEE double, compiled
+ * with -ffp-contract=off so that every product and sum is rounded on its own.
+ *
+ * Storage convention of a lattice state (shared with the CUDA path only as a
+ * documented layout, never as code): 19 planes of nx*ny doubles, plane p at
+ * offset p*nx*ny, cell (x, y) at y*nx + x.  Planes 0..8 are the D2Q9 density
+ * populations f_i; plane 9 + 2k + a is component a (0 = x, 1 = y) of the
+ * D2Q5 vector magnetic population g_k.  The state stored between steps is
+ * the post-collision population at each node (streaming happens at the start
+ * of the next step, by pulling from x - c_i).
+ *
+ * Readings of the paper taken here (where it is silent or garbled):
+ *   - D2Q9 weights {4/9, 1/9, 1/36} and D2Q5 weights {1/3, 1/6}: not stated
+ *     in Sec. 3; these are the only values for which T f^eq reproduces the
+ *     equilibrium-moment table (Eq. KinMomentEq) and T_m g^eq reproduces
+ *     Eq. MagMomentEq.
+ *   - N_{a1}^eq, N_{a2}^eq use u (not rho*u): Eq. MagMomentEq prints rho*u
+ *     but the D2Q5 equilibrium of Sec. 3 and the induction term of
+ *     Eq. FinalMagnetic both give u_x B_a - u_a B_x.
+ *   - Local LES relaxation (the paper gives no local rate; this is its
+ *     MHD-Smagorinsky closure, Eqs. SmagorinskyMHDClosureV/B, applied as an
+ *     eddy increment of the transport coefficients of Sec. 4.3):
+ *       nu_eff  = nu  + C_S Delta^2 |S|,  |S| from the non-equilibrium
+ *                 stress (Sec. 1.2: sum c_a c_b f^(1) = -(rho tau/3)(2 S_ab))
+ *       eta_eff = eta + C_S Delta^2 |j|,  |j| from the antisymmetric part of
+ *                 the non-equilibrium first moment of g, -(tau_m/3) j_z
+ *     with nu = (tau - 1/2)/3 and eta = (tau_m - 1/2)/3 (Sec. 4.3).  The
+ *     implicit dependence on tau is solved exactly (a quadratic in tau).
+ *   - s_5, s_6 default to the base 1/tau_nu, s_7 = s_8 to the local s_nu; any
+ *     positive value given overrides (the paper leaves them free, Sec. 3).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Lattice vectors, Sec. 3 (explicit component lists). */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int MCX[5] = {0, 1, 0, -1, 0};
+static const int MCY[5] = {0, 0, 1, 0, -1};
+
+#define NF 9
+#define NG 5
+#define NPLANE 19
+
+/* Parameter vector passed from the host wrapper (all doubles). */
+enum { P_TAU_NU = 0, P_TAU_ETA, P_CS, P_DELTA, P_S5, P_S6, P_S7, P_S8, P_LES, P_COUNT };
+
+static double w9(int i) {
+    int c2 = CX[i] * CX[i] + CY[i] * CY[i];
+    if (c2 == 0) return 4.0 / 9.0;
+    if (c2 == 1) return 1.0 / 9.0;
+    return 1.0 / 36.0;
+}
+
+static double w5(int k) { return k == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+
+/* T of Eq. FluidTMatrix, built from its row formulas. */
+static void build_T(double T[NF][NF]) {
+    for (int i = 0; i < NF; ++i) {
+        double cx = CX[i], cy = CY[i];
+        double cx2 = cx * cx, cy2 = cy * cy;
+        T[0][i] = 1.0;
+        T[1][i] = cx;
+        T[2][i] = cy;
+        T[3][i] = cx * cy;
+        T[4][i] = cx2 - cy2;
+        T[5][i] = 3.0 * cx * cy2 - 2.0 * cx;
+        T[6][i] = 3.0 * cy * cx2 - 2.0 * cy;
+        T[7][i] = 4.0 - 9.0 * (cx2 + cy2 - 2.0 * cx2 * cy2);
+        T[8][i] = 4.0 - 4.0 * (cx2 + cy2) + 3.0 * cx2 * cy2;
+    }
+}
+
+/* T_m of Eq. MagTMatrix, from its row formulas. */
+static void build_Tm(double Tm[NG][NG]) {
+    for (int k = 0; k < NG; ++k) {
+        double cx = MCX[k], cy = MCY[k];
+        Tm[0][k] = 1.0;
+        Tm[1][k] = cx;
+        Tm[2][k] = cy;
+        Tm[3][k] = cx * cx;
+        Tm[4][k] = cy * cy;
+    }
+}
+
+/* Gauss-Jordan inverse with partial pivoting (the "transform back" of the
+ * MRT step, Sec. 3: relax in moment space, return to distribution space). */
+static int invert(int n, const double* A, double* Ainv) {
+    double a[NF][2 * NF];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            a[r][c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (a[piv][col] == 0.0) return -1;
+        if (piv != col)
+            for (int c = 0; c < 2 * n; ++c) {
+                double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t;
+            }
+        double d = a[col][col];
+        for (int c = 0; c < 2 * n; ++c) a[col][c] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double m = a[r][col];
+            if (m == 0.0) continue;
+            for (int c = 0; c < 2 * n; ++c) a[r][c] -= m * a[col][c];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = a[r][c + n];
+    return 0;
+}
+
+static double g_T[NF][NF], g_Tinv[NF][NF];
+static int g_ready = 0;
+
+static void setup(void) {
+    if (g_ready) return;
+    build_T(g_T);
+    invert(NF, &g_T[0][0], &g_Tinv[0][0]);
+    g_ready = 1;
+}
+
+/* ---- exported: lattice constants and matrices (for pins) --------------- */
+
+void orc_lattice(int* cx, int* cy, int* mcx, int* mcy, double* w, double* wm) {
+    for (int i = 0; i < NF; ++i) { cx[i] = CX[i]; cy[i] = CY[i]; w[i] = w9(i); }
+    for (int k = 0; k < NG; ++k) { mcx[k] = MCX[k]; mcy[k] = MCY[k]; wm[k] = w5(k); }
+}
+
+void orc_tmatrix(double* T, double* Tinv, double* Tm) {
+    setup();
+    double tm[NG][NG];
+    build_Tm(tm);
+    memcpy(T, g_T, sizeof g_T);
+    memcpy(Tinv, g_Tinv, sizeof g_Tinv);
+    memcpy(Tm, tm, sizeof tm);
+}
+
+/* D2Q9 equilibrium, Sec. 3 (f_i^(eq) with the Maxwell-stress term). */
+void orc_feq(double rho, double ux, double uy, double bx, double by, double* f) {
+    double u2 = ux * ux + uy * uy;
+    double b2 = bx * bx + by * by;
+    for (int i = 0; i < NF; ++i) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double cb = CX[i] * bx + CY[i] * by;
+        double c2 = CX[i] * CX[i] + CY[i] * CY[i];
+        double w = w9(i);
+        f[i] = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2)
+             + 4.5 * w * (0.5 * b2 * c2 - cb * cb);
+    }
+}
+
+/* D2Q5 vector equilibrium, Sec. 3; g[2k + a]. */
+void orc_geq(double ux, double uy, double bx, double by, double* g) {
+    double B[2] = {bx, by}, U[2] = {ux, uy};
+    for (int k = 0; k < NG; ++k) {
+        double Cu = MCX[k] * ux + MCY[k] * uy;
+        double CB = MCX[k] * bx + MCY[k] * by;
+        for (int a = 0; a < 2; ++a)
+            g[2 * k + a] = w5(k) * (B[a] + 3.0 * (Cu * B[a] - CB * U[a]));
+    }
+}
+
+/* ---- the collision at one node ------------------------------------------
+ * z: the 19 streamed (pre-collision) populations of the node.
+ * out: the 19 post-collision populations.
+ * aux (optional, 4 doubles): tau_nu_eff, tau_m_eff, Q, J.
+ */
+void orc_collide_cell(const double* z, const double* p, double* out, double* aux) {
+    setup();
+    const double* f = z;
+    const double* g = z + NF;
+    double tau_nu = p[P_TAU_NU], tau_eta = p[P_TAU_ETA];
+    double CS = p[P_CS], delta = p[P_DELTA];
+    int les = p[P_LES] != 0.0;
+
+    /* moments rho, rho u, B (Sec. 3) */
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < NF; ++i) {
+        rho += f[i];
+        jx += CX[i] * f[i];
+        jy += CY[i] * f[i];
+    }
+    double ux = jx / rho, uy = jy / rho;
+    double bx = 0.0, by = 0.0;
+    for (int k = 0; k < NG; ++k) { bx += g[2 * k]; by += g[2 * k + 1]; }
+
+    /* M = T f (Eq. Transformation) */
+    double M[NF];
+    for (int j = 0; j < NF; ++j) {
+        M[j] = 0.0;
+        for (int i = 0; i < NF; ++i) M[j] += g_T[j][i] * f[i];
+    }
+    /* equilibrium moments, Eq. KinMomentEq (written in rho and rho u) */
+    double Meq[NF];
+    Meq[0] = rho;
+    Meq[1] = jx;
+    Meq[2] = jy;
+    Meq[3] = jx * jy / rho - bx * by;
+    Meq[4] = (jx * jx - jy * jy) / rho - bx * bx + by * by;
+    Meq[5] = -jx;
+    Meq[6] = -jy;
+    Meq[7] = -3.0 * (jx * jx + jy * jy) / rho;
+    Meq[8] = 5.0 / 3.0 * rho - 3.0 * (jx * jx + jy * jy) / rho;
+
+    double n[NF];
+    for (int j = 0; j < NF; ++j) n[j] = M[j] - Meq[j];
+
+    /* local eddy relaxation times (reading above) */
+    double tau_e = tau_nu, tau_m = tau_eta, Q = 0.0, J = 0.0;
+    if (les) {
+        /* |S| = 3 Q / (2 rho tau_e), Q = sqrt(n_4^2 + 4 n_3^2);
+         * tau_e = tau_nu + 3 C_S Delta^2 |S|  =>  quadratic in tau_e */
+        Q = sqrt(n[4] * n[4] + 4.0 * n[3] * n[3]);
+        tau_e = 0.5 * (tau_nu + sqrt(tau_nu * tau_nu + 18.0 * CS * delta * delta * Q / rho));
+        /* N = T_m g (Eq. Transformation), rows C_x and C_y; equilibria of
+         * Eq. MagMomentEq with u. |j| = 3 J / tau_m. */
+        double Ny1 = 0.0, Nx2 = 0.0;
+        for (int k = 0; k < NG; ++k) {
+            Ny1 += MCX[k] * g[2 * k + 1];
+            Nx2 += MCY[k] * g[2 * k];
+        }
+        double Ny1eq = ux * by - uy * bx;
+        double Nx2eq = uy * bx - ux * by;
+        J = fabs((Ny1 - Ny1eq) - (Nx2 - Nx2eq));
+        tau_m = 0.5 * (tau_eta + sqrt(tau_eta * tau_eta + 36.0 * CS * delta * delta * J));
+    }
+    double s_nu = 1.0 / tau_e;
+    double s[NF];
+    s[0] = s[1] = s[2] = 0.0; /* conserved: n_0 = n_1 = n_2 = 0 anyway */
+    s[3] = s[4] = s_nu;
+    s[5] = p[P_S5] > 0.0 ? p[P_S5] : 1.0 / tau_nu;
+    s[6] = p[P_S6] > 0.0 ? p[P_S6] : 1.0 / tau_nu;
+    s[7] = p[P_S7] > 0.0 ? p[P_S7] : s_nu;
+    s[8] = p[P_S8] > 0.0 ? p[P_S8] : s_nu;
+
+    /* relax in moment space, return with T^-1 (Sec. 3) */
+    double Ms[NF];
+    for (int j = 0; j < NF; ++j) Ms[j] = M[j] - s[j] * n[j];
+    for (int i = 0; i < NF; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < NF; ++j) acc += g_Tinv[i][j] * Ms[j];
+        out[i] = acc;
+    }
+
+    /* magnetic SRT collision in distribution space (Eq. LBMagEqn) */
+    double geq[2 * NG];
+    orc_geq(ux, uy, bx, by, geq);
+    double sm = 1.0 / tau_m;
+    for (int q = 0; q < 2 * NG; ++q) out[NF + q] = g[q] - sm * (g[q] - geq[q]);
+
+    if (aux) { aux[0] = tau_e; aux[1] = tau_m; aux[2] = Q; aux[3] = J; }
+}
+
+/* ---- lattice-wide operations --------------------------------------------- */
+
+static long wrap(long a, long n) {
+    long r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+static int plane_cx(int p) { return p < NF ? CX[p] : MCX[(p - NF) / 2]; }
+static int plane_cy(int p) { return p < NF ? CY[p] : MCY[(p - NF) / 2]; }
+
+/* Streaming, a pure shift (Sec. 1.2): dst_p(x) = src_p(x - c_p), periodic. */
+void orc_stream(int nx, int ny, const double* src, double* dst) {
+    long N = (long)nx * ny;
+    for (int p = 0; p < NPLANE; ++p) {
+        int cx = plane_cx(p), cy = plane_cy(p);
+        for (long y = 0; y < ny; ++y)
+            for (long x = 0; x < nx; ++x)
+                dst[p * N + y * nx + x] =
+                    src[p * N + wrap(y - cy, ny) * nx + wrap(x - cx, nx)];
+    }
+}
+
+/* Equilibrium initialisation: f = f^eq(rho, u, B), g = g^eq(u, B). */
+void orc_init(int nx, int ny, const double* rho, const double* ux, const double* uy,
+              const double* bx, const double* by, double* state) {
+    long N = (long)nx * ny;
+    double f[NF], g[2 * NG];
+    for (long c = 0; c < N; ++c) {
+        orc_feq(rho[c], ux[c], uy[c], bx[c], by[c], f);
+        orc_geq(ux[c], uy[c], bx[c], by[c], g);
+        for (int i = 0; i < NF; ++i) state[i * N + c] = f[i];
+        for (int q = 0; q < 2 * NG; ++q) state[(NF + q) * N + c] = g[q];
+    }
+}
+
+/* One or more full time steps: stream, then collide at every node.
+ * state (19 planes) is advanced in place; work is a caller buffer of the
+ * same size.  nthreads > 1 splits the collision loop over rows (OpenMP
+ * builds only); results do not depend on it. */
+int orc_step(int nx, int ny, const double* p, double* state, double* work, int nsteps,
+             int nthreads) {
+    setup();
+    long N = (long)nx * ny;
+    (void)nthreads;
+    for (int t = 0; t < nsteps; ++t) {
+        orc_stream(nx, ny, state, work);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
+        for (long y = 0; y < ny; ++y) {
+            double z[NPLANE], o[NPLANE];
+            for (long x = 0; x < nx; ++x) {
+                long c = y * nx + x;
+                for (int q = 0; q < NPLANE; ++q) z[q] = work[q * N + c];
+                orc_collide_cell(z, p, o, NULL);
+                for (int q = 0; q < NPLANE; ++q) state[q * N + c] = o[q];
+            }
+        }
+    }
+    return 0;
+}
+
+/* One step evaluated at selected nodes only: out[c*19 + q] is the
+ * post-collision population q at node idx[c] after streaming from state. */
+void orc_step_cells(int nx, int ny, const double* p, const double* state, long ncells,
+                    const long* idx, double* out) {
+    setup();
+    long N = (long)nx * ny;
+    for (long c = 0; c < ncells; ++c) {
+        long x = idx[c] % nx, y = idx[c] / nx;
+        double z[NPLANE];
+        for (int q = 0; q < NPLANE; ++q)
+            z[q] = state[q * N + wrap(y - plane_cy(q), ny) * nx + wrap(x - plane_cx(q), nx)];
+        orc_collide_cell(z, p, out + c * NPLANE, NULL);
+    }
+}
+
+/* Per-node local LES quantities after streaming (tau_e, tau_m, Q, J). */
+void orc_les_fields(int nx, int ny, const double* p, const double* state, double* aux) {
+    setup();
+    long N = (long)nx * ny;
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            double z[NPLANE], o[NPLANE], a[4];
+            for (int q = 0; q < NPLANE; ++q)
+                z[q] = state[q * N + wrap(y - plane_cy(q), ny) * nx + wrap(x - plane_cx(q), nx)];
+            orc_collide_cell(z, p, o, a);
+            for (int r = 0; r < 4; ++r) aux[r * N + y * nx + x] = a[r];
+        }
+}
+
+/* Moments of a stored state: rho, u, B at every node (Sec. 3). The
+ * collision conserves them, so they are those of the streamed populations
+ * of the step that produced the state. */
+void orc_moments(int nx, int ny, const double* state, double* rho, double* ux, double* uy,
+                 double* bx, double* by) {
+    long N = (long)nx * ny;
+    for (long c = 0; c < N; ++c) {
+        double r = 0.0, jx = 0.0, jy = 0.0, Bx = 0.0, By = 0.0;
+        for (int i = 0; i < NF; ++i) {
+            double fi = state[i * N + c];
+            r += fi; jx += CX[i] * fi; jy += CY[i] * fi;
+        }
+        for (int k = 0; k < NG; ++k) {
+            Bx += state[(NF + 2 * k) * N + c];
+            By += state[(NF + 2 * k + 1) * N + c];
+        }
+        rho[c] = r; ux[c] = jx / r; uy[c] = jy / r; bx[c] = Bx; by[c] = By;
+    }
+}
+
+/* Diagnostics.  out[0..11]:
+ *  0 mass = sum rho            1,2 sum rho u_x, sum rho u_y
+ *  3,4 sum B_x, sum B_y        5 E_K = <rho |u|^2>/2       6 E_M = <|B|^2>/2
+ *  7 enstrophy <omega^2>/2     8 cross helicity <u.B>
+ *  9 max |div B|               10 rms div B                11 <j_z^2>/2
+ * <.> is the mean over nodes; omega, j_z and div B use periodic central
+ * differences (the discrete operator under which the paper's div B = 0
+ * statement is checked). */
+void orc_diagnostics(int nx, int ny, const double* state, double* out) {
+    long N = (long)nx * ny;
+    double* rho = (double*)malloc(sizeof(double) * N * 5);
+    double *ux = rho + N, *uy = rho + 2 * N, *bx = rho + 3 * N, *by = rho + 4 * N;
+    orc_moments(nx, ny, state, rho, ux, uy, bx, by);
+    double s[12];
+    for (int r = 0; r < 12; ++r) s[r] = 0.0;
+    double dmax = 0.0;
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            long c = y * nx + x;
+            long xp = y * nx + wrap(x + 1, nx), xm = y * nx + wrap(x - 1, nx);
+            long yp = wrap(y + 1, ny) * nx + x, ym = wrap(y - 1, ny) * nx + x;
+            s[0] += rho[c];
+            s[1] += rho[c] * ux[c];
+            s[2] += rho[c] * uy[c];
+            s[3] += bx[c];
+            s[4] += by[c];
+            s[5] += rho[c] * (ux[c] * ux[c] + uy[c] * uy[c]);
+            s[6] += bx[c] * bx[c] + by[c] * by[c];
+            double om = 0.5 * (uy[xp] - uy[xm]) - 0.5 * (ux[yp] - ux[ym]);
+            s[7] += om * om;
+            s[8] += ux[c] * bx[c] + uy[c] * by[c];
+            double dv = 0.5 * (bx[xp] - bx[xm]) + 0.5 * (by[yp] - by[ym]);
+            if (fabs(dv) > dmax) dmax = fabs(dv);
+            s[10] += dv * dv;
+            double jz = 0.5 * (by[xp] - by[xm]) - 0.5 * (bx[yp] - bx[ym]);
+            s[11] += jz * jz;
+        }
+    double inv = 1.0 / (double)N;
+    out[0] = s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+    out[3] = s[3];
+    out[4] = s[4];
+    out[5] = 0.5 * s[5] * inv;
+    out[6] = 0.5 * s[6] * inv;
+    out[7] = 0.5 * s[7] * inv;
+    out[8] = s[8] * inv;
+    out[9] = dmax;
+    out[10] = sqrt(s[10] * inv);
+    out[11] = 0.5 * s[11] * inv;
+    free(rho);
+}
+
+/* ---- independent routes used only by pins --------------------------------- */
+
+/* Plain BGK step in distribution space (Sec. 1.2), f and g with their own
+ * single relaxation times and no LES: the special case the MRT step must
+ * reduce to when every rate is tied (Sec. 4.3). */
+int orc_step_bgk(int nx, int ny, double tau_nu, double tau_eta, double* state, double* work,
+                 int nsteps) {
+    long N = (long)nx * ny;
+    for (int t = 0; t < nsteps; ++t) {
+        orc_stream(nx, ny, state, work);
+        for (long c = 0; c < N; ++c) {
+            double f[NF], g[2 * NG], feq[NF], geq[2 * NG];
+            for (int i = 0; i < NF; ++i) f[i] = work[i * N + c];
+            for (int q = 0; q < 2 * NG; ++q) g[q] = work[(NF + q) * N + c];
+            double rho = 0, jx = 0, jy = 0, bx = 0, by = 0;
+            for (int i = 0; i < NF; ++i) { rho += f[i]; jx += CX[i] * f[i]; jy += CY[i] * f[i]; }
+            for (int k = 0; k < NG; ++k) { bx += g[2 * k]; by += g[2 * k + 1]; }
+            orc_feq(rho, jx / rho, jy / rho, bx, by, feq);
+            orc_geq(jx / rho, jy / rho, bx, by, geq);
+            for (int i = 0; i < NF; ++i) state[i * N + c] = f[i] - (f[i] - feq[i]) / tau_nu;
+            for (int q = 0; q < 2 * NG; ++q)
+                state[(NF + q) * N + c] = g[q] - (g[q] - geq[q]) / tau_eta;
+        }
+    }
+    return 0;
+}

@@ -1,0 +1,519 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a matrix
+or list printed in the paper (tests/golden), a second statement of the same
+quantity elsewhere in the paper (the equilibrium-moment tables), a textbook
+special case (BGK), a closed-form decay or dispersion relation derived from
+the paper's transport coefficients (Sec. 4.3), a symmetry, or a brute-force
+construction.  A dropped term, a wrong sign or index, or a transposed
+operand anywhere in the oracle fails at least one of them.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from conftest import load_golden
+from paper_1607_08675_gb300 import inputs
+
+# ---------------------------------------------------------------- constants
+
+
+def test_lattice_vectors_match_paper(orc):
+    """Sec. 3: explicit component lists of c_i and C_k."""
+    g = {r[0]: [int(v) for v in r[1:]] for r in load_golden("lattice_vectors.txt")}
+    cx, cy, mx, my, w, wm = orc.lattice()
+    assert list(cx) == g["cx"] and list(cy) == g["cy"]
+    assert list(mx) == g["Cx"] and list(my) == g["Cy"]
+
+
+def test_T_built_from_row_formulas_equals_printed_matrix(orc):
+    """Eq. FluidTMatrix and Eq. MagTMatrix: the oracle builds T and T_m from
+    the symbolic rows; they must equal the printed numeric matrices."""
+    T, Ti, Tm = orc.tmatrix()
+    Tg = np.array(load_golden("T_matrix.txt"), dtype=float)
+    Tmg = np.array(load_golden("Tm_matrix.txt"), dtype=float)
+    assert np.array_equal(T, Tg)
+    assert np.array_equal(Tm, Tmg)
+
+
+def test_T_inverse_and_orthogonality(orc):
+    """The rows of T are mutually orthogonal, so T^-1 = T^t diag(1/|T_j|^2)
+    exactly; the oracle's numerically inverted T must agree."""
+    T, Ti, _ = orc.tmatrix()
+    G = T @ T.T
+    assert np.array_equal(G, np.diag(np.diag(G)))
+    assert list(np.diag(G)) == [9, 6, 6, 4, 4, 12, 12, 180, 20]
+    exact = T.T / np.diag(G)[None, :]
+    assert np.max(np.abs(Ti - exact)) < 1e-15
+    assert np.max(np.abs(Ti @ T - np.eye(9))) < 1e-15
+
+
+def _rand_fields(rng):
+    rho = rng.uniform(0.7, 1.4)
+    ux, uy, bx, by = rng.uniform(-0.2, 0.2, size=4)
+    return rho, ux, uy, bx, by
+
+
+def test_feq_reproduces_equilibrium_moment_table(orc):
+    """Sec. 3: T f^eq (with the D2Q9 weights, which the paper does not print)
+    must equal the table Eq. KinMomentEq, written in rho and rho u."""
+    T, _, _ = orc.tmatrix()
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        rho, ux, uy, bx, by = _rand_fields(rng)
+        jx, jy = rho * ux, rho * uy
+        M = T @ orc.feq(rho, ux, uy, bx, by)
+        table = [rho, jx, jy,
+                 jx * jy / rho - bx * by,
+                 (jx * jx - jy * jy) / rho - bx * bx + by * by,
+                 -jx, -jy,
+                 -3.0 * (jx * jx + jy * jy) / rho,
+                 5.0 / 3.0 * rho - 3.0 * (jx * jx + jy * jy) / rho]
+        assert np.max(np.abs(M - np.array(table))) < 1e-14
+
+
+def test_feq_second_moment_is_momentum_flux_with_maxwell_stress(orc):
+    """The D2Q9 equilibrium's second moment is p I + rho u u + |B|^2/2 I - B B
+    with p = rho/3 (Sec. 4.3 equation of state, Eq. FinalMomentum)."""
+    cx, cy, *_ = orc.lattice()
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        rho, ux, uy, bx, by = _rand_fields(rng)
+        f = orc.feq(rho, ux, uy, bx, by)
+        c = np.stack([cx, cy]).astype(float)
+        Pi = np.einsum("ai,bi,i->ab", c, c, f)
+        u, B = np.array([ux, uy]), np.array([bx, by])
+        ref = (rho / 3 + 0.5 * B @ B) * np.eye(2) + rho * np.outer(u, u) - np.outer(B, B)
+        assert np.max(np.abs(Pi - ref)) < 1e-15
+
+
+def test_geq_reproduces_magnetic_moment_table(orc):
+    """Sec. 3: T_m g^eq must equal Eq. MagMomentEq.  The table prints
+    rho u in N_a1, N_a2 while the D2Q5 equilibrium has u; with rho != 1 only
+    the u reading holds, which is the one the oracle takes."""
+    _, _, Tm = orc.tmatrix()
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        rho, ux, uy, bx, by = _rand_fields(rng)
+        g = orc.geq(ux, uy, bx, by)  # (5, 2)
+        N = Tm @ g  # N[k, a]
+        B, u = np.array([bx, by]), np.array([ux, uy])
+        assert np.max(np.abs(N[0] - B)) < 1e-16
+        assert np.max(np.abs(N[1] - (ux * B - u * bx))) < 1e-16
+        assert np.max(np.abs(N[2] - (uy * B - u * by))) < 1e-16
+        assert np.max(np.abs(N[3] - B / 3)) < 1e-16
+        assert np.max(np.abs(N[4] - B / 3)) < 1e-16
+
+
+# ---------------------------------------------------------------- collision
+
+PRESETS = {
+    "tied": dict(tau_nu=0.6, tau_eta=0.6, C_S=0.1),
+    "mrt": dict(tau_nu=0.6, tau_eta=0.7, C_S=0.1, s5=1.2, s6=1.2, s7=1.3, s8=1.3),
+}
+
+
+def _noneq_state(orc, nx, ny, seed):
+    rho, ux, uy, bx, by = inputs.orszag_tang(nx, ny, amp=1e-3, seed=seed)
+    st = orc.init(rho, ux, uy, bx, by)
+    rng = np.random.default_rng(seed)
+    return st + 1e-4 * rng.standard_normal(st.shape)
+
+
+@pytest.mark.parametrize("preset", list(PRESETS))
+def test_collision_invariants_per_node(orc, preset):
+    """Sec. 3: M_0, M_1, M_2 and N_a0 are collision invariants."""
+    p = orc.params(**PRESETS[preset])
+    cx, cy, *_ = orc.lattice()
+    rng = np.random.default_rng(1)
+    st = _noneq_state(orc, 4, 4, 2)
+    for c in range(16):
+        z = st[:, c // 4, c % 4] + 1e-3 * rng.standard_normal(19)
+        out, _ = orc.collide_cell(z, p)
+        for vec in (np.ones(9), cx, cy):
+            assert abs(vec @ out[:9] - vec @ z[:9]) < 1e-15
+        assert np.max(np.abs(out[9:].reshape(5, 2).sum(0) - z[9:].reshape(5, 2).sum(0))) < 1e-16
+
+
+def test_collision_matches_library_solve_route(orc):
+    """Moment-space relaxation returned to distribution space with a library
+    linear solve on the printed T (Sec. 3), rates s5..s8 all distinct: the
+    oracle's collision must agree."""
+    Tg = np.array(load_golden("T_matrix.txt"), dtype=float)
+    p = orc.params(tau_nu=0.6, tau_eta=0.7, C_S=0.0, les=0, s5=1.1, s6=1.25, s7=1.3, s8=1.45)
+    rng = np.random.default_rng(9)
+    st = _noneq_state(orc, 3, 3, 4)
+    for c in range(9):
+        z = st[:, c // 3, c % 3]
+        out, _ = orc.collide_cell(z, p)
+        f = z[:9]
+        M = Tg @ f
+        rho, jx, jy = M[0], M[1], M[2]
+        B = z[9:].reshape(5, 2).sum(0)
+        Meq = M.copy()
+        Meq[3] = jx * jy / rho - B[0] * B[1]
+        Meq[4] = (jx * jx - jy * jy) / rho - B[0] ** 2 + B[1] ** 2
+        Meq[5], Meq[6] = -jx, -jy
+        Meq[7] = -3 * (jx * jx + jy * jy) / rho
+        Meq[8] = 5 / 3 * rho - 3 * (jx * jx + jy * jy) / rho
+        s = np.array([0, 0, 0, 1 / 0.6, 1 / 0.6, 1.1, 1.25, 1.3, 1.45])
+        fs = np.linalg.solve(Tg, M - s * (M - Meq))
+        assert np.max(np.abs(out[:9] - fs)) < 1e-15
+
+
+def test_mrt_with_tied_rates_equals_bgk(orc):
+    """Sec. 4.3: with all rates equal the MRT step is the single-relaxation
+    (BGK) update of Sec. 1.2, for f and for the magnetic g."""
+    st = _noneq_state(orc, 12, 10, 6)
+    p = orc.params(tau_nu=0.7, tau_eta=0.9, C_S=0.0, les=0)
+    a = orc.step(st, p, 30)
+    b = orc.step_bgk(st, 0.7, 0.9, 30)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_cs_zero_is_bitwise_les_off(orc):
+    """C_S = 0 must leave the relaxation times exactly at their base values
+    (sqrt of a rounded square is exact), so LES on with C_S = 0 reproduces
+    the plain MRT step bit for bit."""
+    st = _noneq_state(orc, 9, 7, 1)
+    a = orc.step(st, orc.params(C_S=0.0, les=1), 10)
+    b = orc.step(st, orc.params(C_S=0.0, les=0), 10)
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- streaming
+
+
+def test_stream_moves_a_spike_along_each_lattice_vector(orc):
+    """Streaming is a shift by c_i (Sec. 1.2) with periodic wrap."""
+    cx, cy, mx, my, *_ = orc.lattice()
+    nx, ny = 5, 3
+    pcx = list(cx) + [mx[k] for k in range(5) for _ in range(2)]
+    pcy = list(cy) + [my[k] for k in range(5) for _ in range(2)]
+    for (x0, y0) in ((0, 0), (4, 2), (2, 1)):
+        st = np.zeros((19, ny, nx))
+        st[:, y0, x0] = 1.0
+        out = orc.stream(st)
+        for p in range(19):
+            exp = np.zeros((ny, nx))
+            exp[(y0 + pcy[p]) % ny, (x0 + pcx[p]) % nx] = 1.0
+            assert np.array_equal(out[p], exp), p
+
+
+def test_uniform_state_stays_uniform(orc):
+    rng = np.random.default_rng(0)
+    rho, ux, uy, bx, by = _rand_fields(rng)
+    one = np.ones((4, 6))
+    st = orc.init(rho * one, ux * one, uy * one, bx * one, by * one)
+    out = orc.step(st, orc.params(**PRESETS["mrt"]), 5)
+    assert np.all(out == out[:, :1, :1])
+    assert np.max(np.abs(out - st)) < 1e-15
+
+
+def test_translation_equivariance_bitwise(orc):
+    st = _noneq_state(orc, 8, 6, 3)
+    p = orc.params(**PRESETS["mrt"])
+    a = np.roll(orc.step(st, p, 4), (2, 3), axis=(1, 2))
+    b = orc.step(np.roll(st, (2, 3), axis=(1, 2)), p, 4)
+    assert np.array_equal(a, b)
+
+
+# 90 degree rotation c -> (-c_y, c_x) as a permutation of population indices
+ROT9 = [0, 2, 3, 4, 1, 6, 7, 8, 5]
+ROT5 = [0, 2, 3, 4, 1]
+
+
+def _rotate(st):
+    """Rotate a square-lattice state by +90 degrees: node (x, y) moves to
+    (-y, x); population i moves to ROT9[i]; vector g components rotate."""
+    n = st.shape[1]
+    out = np.empty_like(st)
+    ys, xs = np.mgrid[0:n, 0:n]
+    nx_, ny_ = (-ys) % n, xs
+    for i in range(9):
+        out[ROT9[i], ny_, nx_] = st[i, ys, xs]
+    for k in range(5):
+        gx, gy = st[9 + 2 * k], st[10 + 2 * k]
+        kk = ROT5[k]
+        out[9 + 2 * kk, ny_, nx_] = -gy[ys, xs]
+        out[10 + 2 * kk, ny_, nx_] = gx[ys, xs]
+    return out
+
+
+def test_rotation_equivariance_with_swapped_flux_rates(orc):
+    """A 90 degree rotation exchanges the x and y energy-flux moments M_5 and
+    M_6, so rotating the state must commute with the step once s5 and s6 are
+    swapped; this pins every direction-dependent sign and index."""
+    st = _noneq_state(orc, 8, 8, 8)
+    pa = orc.params(tau_nu=0.6, tau_eta=0.7, C_S=0.2, s5=1.1, s6=1.4, s7=1.3, s8=1.2)
+    pb = orc.params(tau_nu=0.6, tau_eta=0.7, C_S=0.2, s5=1.4, s6=1.1, s7=1.3, s8=1.2)
+    a = _rotate(orc.step(st, pa, 6))
+    b = orc.step(_rotate(st), pb, 6)
+    assert np.max(np.abs(a - b)) < 1e-15
+    # and the unswapped rates must not commute (the test has teeth)
+    c = orc.step(_rotate(st), pa, 6)
+    assert np.max(np.abs(a - c)) > 1e-9
+
+
+# ---------------------------------------------------------------- conservation
+
+
+def test_global_invariants_conserved_over_200_steps(orc):
+    """Sec. 3 collision invariants + periodic streaming: total mass,
+    momentum and magnetic field are constant."""
+    rho, ux, uy, bx, by = inputs.orszag_tang(32, 32, seed=2)
+    st = orc.init(rho, ux, uy, bx, by)
+    d0 = orc.diagnostics(st)
+    d1 = orc.diagnostics(orc.step(st, orc.params(**PRESETS["mrt"]), 200))
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    for k in ("mom_x", "mom_y", "bsum_x", "bsum_y"):
+        assert abs(d1[k] - d0[k]) < 1e-13 * d0["mass"]
+
+
+def test_init_moments_roundtrip(orc):
+    f = inputs.turbulence(24, 20, kmin=2, kmax=4, seed=3)
+    st = orc.init(*f)
+    for a, b in zip(orc.moments(st), f):
+        assert np.max(np.abs(a - b)) < 1e-15
+
+
+# ---------------------------------------------------------------- transport (Sec. 4.3)
+
+
+def _decay_rate(orc, n, p, field, t1, t2):
+    """Measured exponential decay rate / k^2 of a single sine mode."""
+    s = np.sin(2 * np.pi * np.arange(n) / n)
+    z = np.zeros((n, 1)) if field == "ux" else np.zeros((1, n))
+    one = np.ones_like(z)
+    if field == "ux":
+        st = orc.init(one, 1e-6 * s[:, None], z, z, z)
+        amp = lambda q: 2 * np.mean(orc.moments(q)[1][:, 0] * s)
+    else:
+        st = orc.init(one, z, z, z, 1e-6 * s[None, :])
+        amp = lambda q: 2 * np.mean(orc.moments(q)[4][0] * s)
+    a = orc.step(st, p, t1)
+    b = orc.step(a, p, t2 - t1)
+    k = 2 * np.pi / n
+    return -np.log(amp(b) / amp(a)) / (t2 - t1) / (k * k)
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2])
+def test_shear_wave_decays_with_paper_viscosity(orc, tau):
+    """Sec. 4.3: nu = 1/(3 s_3) - 1/6.  A shear wave decays as exp(-nu k^2 t);
+    the lattice error is second order in k."""
+    p = orc.params(tau_nu=tau, tau_eta=0.6, les=0, C_S=0.0)
+    nu = (tau - 0.5) / 3
+    e32 = _decay_rate(orc, 32, p, "ux", 20, 327) / nu - 1
+    e64 = _decay_rate(orc, 64, p, "ux", 20, 1248) / nu - 1
+    assert abs(e64) < 1.5e-3
+    assert 3.0 < e32 / e64 < 5.0
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.9])
+def test_magnetic_mode_decays_with_paper_resistivity(orc, tau):
+    """Sec. 4.3: eta = 1/(3 s_m) - 1/6."""
+    p = orc.params(tau_nu=0.7, tau_eta=tau, les=0, C_S=0.0)
+    eta = (tau - 0.5) / 3
+    e32 = _decay_rate(orc, 32, p, "by", 20, 327) / eta - 1
+    e64 = _decay_rate(orc, 64, p, "by", 20, 1248) / eta - 1
+    assert abs(e64) < 1.5e-3
+    assert abs(e64) < abs(e32) / 2.5 or abs(e32) < 1e-5
+
+
+def _linear_mode_error(orc, n, p, fields, A, T, comps):
+    """Max error (relative to the initial amplitude) of a single Fourier mode
+    against exp(A t) over 8 sample times."""
+    x = 2 * np.pi * np.arange(n) / n
+    st = orc.init(*[f[None, :] for f in fields])
+    a0 = np.array([c(orc.moments(st), x) for c in comps])
+    amp = np.max(np.abs(a0))
+    err, t, s = 0.0, 0, st
+    for tt in np.linspace(0, T, 9)[1:].astype(int):
+        s = orc.step(s, p, tt - t)
+        t = tt
+        got = np.array([c(orc.moments(s), x) for c in comps])
+        err = max(err, np.max(np.abs(got - expm(A * t) @ a0)) / amp)
+    return err
+
+
+def test_alfven_wave_dispersion(orc):
+    """Linearised Eqs. FinalMomentum and FinalMagnetic (rho = 1, uniform
+    B_0 along x, transverse mode e^{ikx}): d/dt (u_y, b_y) =
+    [[-nu k^2, i k B_0], [i k B_0, -eta k^2]] (u_y, b_y).  Pins the Lorentz
+    force and the induction term of both equilibria."""
+    tn, te, B0 = 0.6, 0.7, 0.05
+    nu, eta = (tn - 0.5) / 3, (te - 0.5) / 3
+    p = orc.params(tau_nu=tn, tau_eta=te, les=0, C_S=0.0)
+    comps = [lambda m, x: 2 * np.mean(m[2][0] * np.exp(-1j * x)),
+             lambda m, x: 2 * np.mean(m[4][0] * np.exp(-1j * x))]
+    errs = {}
+    for n in (16, 32):
+        x = 2 * np.pi * np.arange(n) / n
+        k = 2 * np.pi / n
+        A = np.array([[-nu * k * k, 1j * k * B0], [1j * k * B0, -eta * k * k]])
+        z = np.zeros(n)
+        fields = (1 + z, z, 1e-6 * np.cos(x), B0 + z, z)
+        errs[n] = _linear_mode_error(orc, n, p, fields, A, int(n / B0), comps)
+    assert errs[32] < 3e-3
+    assert errs[32] < errs[16] / 3
+    # a flipped Lorentz-force sign gives an O(1) error
+    n, k = 32, 2 * np.pi / 32
+    x = 2 * np.pi * np.arange(n) / n
+    Abad = np.array([[-nu * k * k, -1j * k * B0], [1j * k * B0, -eta * k * k]])
+    z = np.zeros(n)
+    bad = _linear_mode_error(orc, n, p, (1 + z, z, 1e-6 * np.cos(x), B0 + z, z), Abad,
+                             int(n / B0), comps)
+    assert bad > 0.5
+
+
+@pytest.mark.parametrize("rates", [(0, 0, 0, 0), (1.2, 1.2, 1.3, 1.3), (1.2, 1.2, 1.1, 1.5)])
+def test_sound_wave_damping_matches_paper_bulk_viscosity(orc, rates):
+    """Sec. 4.3: the longitudinal mode is damped by (xi + 4 nu / 3) k^2 / 2
+    with xi = -1/9 - 1/(9 s_4) - 1/(15 s_7) + 2/(5 s_8) and c_s^2 = 1/3.
+    Pins how s_7 and s_8 enter the collision."""
+    tn = 0.6
+    s5, s6, s7, s8 = rates
+    p = orc.params(tau_nu=tn, tau_eta=0.6, les=0, C_S=0.0, s5=s5, s6=s6, s7=s7, s8=s8)
+    s4 = 1 / tn
+    s7e, s8e = (s7 or s4), (s8 or s4)
+    xi = -1 / 9 - 1 / (9 * s4) - 1 / (15 * s7e) + 2 / (5 * s8e)
+    nu = (tn - 0.5) / 3
+    comps = [lambda m, x: 2 * np.mean((m[0][0] - 1) * np.exp(-1j * x)),
+             lambda m, x: 2 * np.mean(m[0][0] * m[1][0] * np.exp(-1j * x))]
+    errs = {}
+    for n in (32, 64):
+        x = 2 * np.pi * np.arange(n) / n
+        k = 2 * np.pi / n
+        A = np.array([[0, -1j * k], [-1j * k / 3, -(xi + 4 * nu / 3) * k * k]])
+        z = np.zeros(n)
+        errs[n] = _linear_mode_error(orc, n, p, (1 + 1e-6 * np.cos(x), z, z, z, z), A,
+                                     int(4 * n * np.sqrt(3)), comps)
+    assert errs[64] < 4e-3
+    assert errs[64] < errs[32] / 2.5
+
+
+# ---------------------------------------------------------------- LES closure
+
+
+def _dissipation(orc, n, p, kind, amp, t0):
+    """Measured dE/dt against the Smagorinsky prediction
+    -<(nu + C_S Delta^2 |g|) g^2>, g = du_x/dy (or dB_y/dx)."""
+    x = 2 * np.pi * np.arange(n) / n
+    s = amp * np.sin(x)
+    if kind == "shear":
+        z = np.zeros((n, 1))
+        st = orc.init(1 + z, s[:, None], z, z, z)
+        field = lambda q: orc.moments(q)[1][:, 0]
+        energy = lambda q: np.mean(0.5 * orc.moments(q)[0][:, 0] * field(q) ** 2)
+        base = (p["tau_nu"] - 0.5) / 3
+    else:
+        z = np.zeros((1, n))
+        st = orc.init(1 + z, z, z, z, s[None, :])
+        field = lambda q: orc.moments(q)[4][0]
+        energy = lambda q: np.mean(0.5 * field(q) ** 2)
+        base = (p["tau_eta"] - 0.5) / 3
+    s0 = orc.step(st, p, t0 - 1)
+    s1 = orc.step(s0, p, 1)
+    s2 = orc.step(s1, p, 1)
+    dEdt = (energy(s2) - energy(s0)) / 2
+    kk = np.fft.fftfreq(n, 1.0 / n) * 2 * np.pi / n
+    g = np.real(np.fft.ifft(1j * kk * np.fft.fft(field(s1))))
+    pred = -np.mean((base + p["C_S"] * p["delta"] ** 2 * np.abs(g)) * g * g)
+    pred_off = -np.mean(base * g * g)
+    return dEdt / pred - 1, dEdt / pred_off - 1
+
+
+def test_les_eddy_viscosity_dissipation(orc):
+    """Eq. SmagorinskyClosure: nu_T = C_S Delta^2 |S|, with |S| estimated
+    locally from the non-equilibrium stress (Sec. 1.2).  The energy of a
+    shear flow must drain at <(nu + nu_T) |S|^2>."""
+    p = orc.params(tau_nu=0.55, tau_eta=0.6, C_S=0.1, delta=2.0, les=1)
+    e64, off64 = _dissipation(orc, 64, p, "shear", 0.05, 30)
+    e128, _ = _dissipation(orc, 128, p, "shear", 0.05, 30)
+    assert abs(e64) < 4e-3 and abs(e128) < 1.5e-3
+    assert off64 > 0.05  # the eddy term is a visible share
+
+
+def test_les_eddy_resistivity_dissipation(orc):
+    """Eq. SmagorinskyMHDClosureB: eta_t = C_S Delta^2 |j|, with |j| estimated
+    from the antisymmetric non-equilibrium first moment of g."""
+    p = orc.params(tau_nu=0.8, tau_eta=0.6, C_S=1.0, delta=4.0, les=1)
+    e64, off64 = _dissipation(orc, 64, p, "mag", 0.005, 60)
+    e128, _ = _dissipation(orc, 128, p, "mag", 0.005, 60)
+    assert abs(e64) < 4e-3 and abs(e128) < 1.5e-3
+    assert off64 > 0.1
+
+
+def test_local_strain_and_current_estimates(orc):
+    """Sec. 1.2: sum c_a c_b f^(1) = -(rho tau / 3)(d_a u_b + d_b u_a) gives
+    |S| = 3 Q / (2 rho tau); the magnetic analogue gives |j| = 3 J / tau_m."""
+    n = 64
+    x = 2 * np.pi * np.arange(n) / n
+    k = 2 * np.pi / n
+    p = orc.params(tau_nu=0.7, tau_eta=0.8, C_S=0.0, les=1)
+    z = np.zeros((n, 1))
+    st = orc.step(orc.init(1 + z, 1e-3 * np.sin(x)[:, None], z, z, z), p, 40)
+    aux = orc.les_fields(st, p)
+    u = orc.moments(st)[1][:, 0]
+    amp = 2 * np.mean(u * np.sin(x))
+    S = 3 * aux[2][:, 0] / (2 * aux[0][:, 0])
+    assert np.max(np.abs(S - np.abs(amp * k * np.cos(x)))) < 5e-3 * amp * k
+    z = np.zeros((1, n))
+    st = orc.step(orc.init(1 + z, z, z, z, 1e-3 * np.sin(x)[None, :]), p, 40)
+    aux = orc.les_fields(st, p)
+    b = 2 * np.mean(orc.moments(st)[4][0] * np.sin(x))
+    j = 3 * aux[3][0] / aux[1][0]
+    assert np.max(np.abs(j - np.abs(b * k * np.cos(x)))) < 5e-3 * b * k
+
+
+# ---------------------------------------------------------------- div B
+
+
+def test_div_b_machine_zero_when_magnetic_rate_is_one(orc):
+    """Sec. 1.2 claims div B = 0 to machine accuracy.  For periodic central
+    differences this holds exactly when s_m = 1 (no magnetic non-equilibrium
+    memory): the ideal induction fluxes cancel because D_x D_y = D_y D_x."""
+    st = orc.init(*inputs.orszag_tang(32, 32, seed=5))
+    p = orc.params(tau_nu=0.6, tau_eta=1.0, C_S=0.0, les=0)
+    scale = 0.05 * 2 * (2 * np.pi / 32)  # ~ max |grad B|
+    for _ in range(5):
+        st = orc.step(st, p, 20)
+        assert orc.diagnostics(st)["divB_max"] < 1e-13 * scale
+    # with s_m != 1 the magnetic non-equilibrium part streams on and div B
+    # sits at truncation level (a few percent of |grad B| at 32^2): far
+    # above round-off, bounded, not growing
+    st2 = orc.init(*inputs.orszag_tang(32, 32, seed=5))
+    d = []
+    for _ in range(3):
+        st2 = orc.step(st2, orc.params(tau_eta=0.6), 100)
+        d.append(orc.diagnostics(st2)["divB_max"])
+    assert all(1e-8 * scale < v < 0.05 * scale for v in d)
+    assert d[2] < 1.5 * d[0]
+
+
+# ---------------------------------------------------------------- diagnostics
+
+
+def test_diagnostics_closed_forms(orc):
+    """Unperturbed Orszag-Tang on n x n: discrete means of sin^2 over full
+    periods are 1/2, and central differences of sin(m x) are sin(m h) cos(m x)."""
+    n, u0, b0 = 48, 0.05, 0.03
+    st = orc.init(*inputs.orszag_tang(n, n, u0=u0, b0=b0, amp=0.0))
+    d = orc.diagnostics(st)
+    h = 2 * np.pi / n
+    assert abs(d["mass"] - n * n) < 1e-11
+    assert abs(d["E_kin"] - 0.5 * u0 ** 2) < 1e-16
+    assert abs(d["E_mag"] - 0.5 * b0 ** 2) < 1e-16
+    assert abs(d["cross_helicity"] - 0.5 * u0 * b0) < 1e-16
+    assert abs(d["enstrophy"] - 0.5 * u0 ** 2 * np.sin(h) ** 2) < 1e-16
+    assert abs(d["current_sq"] - 0.25 * b0 ** 2 * (np.sin(2 * h) ** 2 + np.sin(h) ** 2)) < 1e-16
+    assert d["divB_max"] < 1e-17 and abs(d["mom_x"]) < 1e-14 and abs(d["bsum_y"]) < 1e-14
+
+
+def test_step_cells_matches_full_step(orc):
+    st = _noneq_state(orc, 11, 7, 12)
+    p = orc.params(**PRESETS["mrt"])
+    full = orc.step(st, p, 1)
+    idx = np.array([0, 5, 10, 11, 40, 76])
+    got = orc.step_cells(st, p, idx)
+    assert np.array_equal(got, full.reshape(19, -1)[:, idx].T)
