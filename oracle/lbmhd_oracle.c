@@ -94,8 +94,8 @@ static void build_Tm(double Tm[NG][NG]) {
     }
 }
 
-/* Gauss-Jordan inverse with partial pivoting (the "transform back" of the
- * MRT step, Sec. 3: relax in moment space, return to distribution space). */
+/* Gauss-Jordan inverse with partial pivoting; exported for the pins (the
+ * step applies the exact orthogonal inverse instead, see orc_collide_cell). */
 static int invert(int n, const double* A, double* Ainv) {
     double a[NF][2 * NF];
     for (int r = 0; r < n; ++r)
@@ -124,13 +124,17 @@ static int invert(int n, const double* A, double* Ainv) {
     return 0;
 }
 
-static double g_T[NF][NF], g_Tinv[NF][NF];
+static double g_T[NF][NF], g_Tinv[NF][NF], g_norm2[NF];
 static int g_ready = 0;
 
 static void setup(void) {
     if (g_ready) return;
     build_T(g_T);
     invert(NF, &g_T[0][0], &g_Tinv[0][0]);
+    for (int j = 0; j < NF; ++j) {
+        g_norm2[j] = 0.0;
+        for (int i = 0; i < NF; ++i) g_norm2[j] += g_T[j][i] * g_T[j][i];
+    }
     g_ready = 1;
 }
 
@@ -248,12 +252,15 @@ void orc_collide_cell(const double* z, const double* p, double* out, double* aux
     s[7] = p[P_S7] > 0.0 ? p[P_S7] : s_nu;
     s[8] = p[P_S8] > 0.0 ? p[P_S8] : s_nu;
 
-    /* relax in moment space, return with T^-1 (Sec. 3) */
+    /* relax in moment space, return with T^-1 (Sec. 3).  The rows of T are
+     * mutually orthogonal, so T^-1 = T^t diag(1/|T_j|^2) exactly; each term is
+     * divided by the exact integer |T_j|^2 (a numerically inverted T is off
+     * by an ulp and biases the populations a little every step). */
     double Ms[NF];
     for (int j = 0; j < NF; ++j) Ms[j] = M[j] - s[j] * n[j];
     for (int i = 0; i < NF; ++i) {
         double acc = 0.0;
-        for (int j = 0; j < NF; ++j) acc += g_Tinv[i][j] * Ms[j];
+        for (int j = 0; j < NF; ++j) acc += g_T[j][i] * Ms[j] / g_norm2[j];
         out[i] = acc;
     }
 
