@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused LB-MHD stream-collide step (MLUPS and fraction of
+the HBM roofline).
+
+Workload (default): decaying 2D MHD turbulence on an 8192 x 8192 periodic
+lattice (random-phase modes 4 <= |k| <= 8, rms 0.04, C_S = 0.1,
+tau = 0.51), FP32 storage and arithmetic, 500 steps timed after warm-up.
+The state (10 GB per buffer) is far larger than L2, so no flush is needed
+between steps.  The same run also times the FP64, FP32-deviation and
+FP16-deviation storage forms on the same lattice (fewer steps), an
+end-to-end pass through the host C ABI (host fields in, host moments
+out), and the CPU oracle on a bounded sample.
+
+One JSON line is printed by rank 0.  Under torchrun each rank advances its
+own independent lattice (different seed; weak scaling, no data exchange);
+the timed region is bracketed by a barrier and the maximum over ranks is
+reported.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded
+sample (a 512 x 512 lattice of the same recipe) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of GB300 HBM roofline, plain FP64 vs FP32/batched vs FP64 oracle"
+WORKLOAD = "decaying 2D MHD turbulence 8192x8192, modes 4<=|k|<=8 rms 0.04, C_S=0.1, tau=0.51"
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp32_dev": "f32 (f32 deviation storage)",
+          "fp16_dev": "f32 (f16 deviation storage)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str):
+        self.dev_id = dev_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev_id, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dev_id_for_smi():
+    import torch
+
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis if vis.isdigit() else "0"
+
+
+def cpu_count():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(budget_s: float = 15.0, n: int = 512):
+    """The FP64 CPU oracle, as it stands, on an n x n lattice of the same
+    recipe, all host cores; returns (MLUPS, steps, cores)."""
+    from oracle import oracle
+    from paper_1607_08675_gb300 import inputs
+
+    oracle.build()
+    cores = cpu_count()
+    st = oracle.init(*inputs.turbulence(n, n, seed=1))
+    p = oracle.params(tau_nu=0.51, tau_eta=0.51, C_S=0.1)
+    t0 = time.perf_counter()
+    st = oracle.step(st, p, 1, nthreads=cores)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.step(st, p, steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, steps, cores, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host
+    cores.  One bench step is one oracle step on a sample lattice of the
+    same recipe, sized so that the whole --warmup W --steps K run takes about
+    two minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1607_08675_gb300 import inputs
+
+    oracle.build()
+    cores = cpu_count()
+    p = oracle.params(tau_nu=0.51, tau_eta=0.51, C_S=0.1)
+    per_step = min(0.5, 120.0 / max(1, args.steps + args.warmup))
+    probe = oracle.init(*inputs.turbulence(128, 128, seed=1))
+    t0 = time.perf_counter()
+    oracle.step(probe, p, 2, nthreads=cores)
+    rate = 2 * 128 * 128 / (time.perf_counter() - t0)  # node updates per second
+    n = int((rate * per_step) ** 0.5) // 32 * 32
+    n = max(32, min(1024, n))
+    st = oracle.init(*inputs.turbulence(n, n, seed=1))
+    st = oracle.step(st, p, args.warmup, nthreads=cores)
+    t0 = time.perf_counter()
+    oracle.step(st, p, args.steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = n * n * args.steps / dt / 1e6
+    sample = (f"{n}x{n} lattice of the same turbulence recipe per step (the 8192^2 "
+              f"lattice does not fit the oracle's time budget), FP64 oracle, {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def make_fields(n, seed):
+    from paper_1607_08675_gb300 import inputs
+
+    return inputs.turbulence(n, n, seed=seed)
+
+
+def timed_steps(L, h, stream, steps, warmup):
+    """Device time (s) of `steps` steps on the handle's stream, after warm-up."""
+    import torch
+
+    L.lbmhd_step(h, warmup)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.lbmhd_step(h, steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1607_08675_gb300 import build, lbmhd as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    L.lib()
+
+    n = args.n
+    fields = make_fields(n, seed=1 + rank)
+    stream = torch.cuda.Stream()
+    kw = dict(tau_nu=0.51, tau_eta=0.51, C_S=0.1, stream=stream)
+    hbm, peak_kind = peaks()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: the chosen precision -----------------------------------
+    prec = args.precision
+    h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, args.warmup)
+    barrier()
+    launches0 = L.lbmhd_launch_count(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_id_for_smi()) as clk:
+        barrier()
+        e0.record(stream)
+        L.lbmhd_step(h, args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+    dt = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    launches = L.lbmhd_launch_count(h) - launches0
+    L.lbmhd_sync(h)
+    cells = n * n
+    value = world * cells * args.steps / dt / 1e6
+    bpc = L.lbmhd_bytes_per_cell(prec)
+    per_launch_s = (e0.elapsed_time(e1) / 1e3) / args.steps
+    achieved = bpc * cells / per_launch_s / 1e9
+    L.lbmhd_destroy(h)
+    del h
+
+    # ---- other storage forms on the same lattice ---------------------------
+    variants = {}
+    if not args.no_variants:
+        for vp, vsteps in (("fp64", args.steps // 10), ("fp32_dev", args.steps),
+                           ("fp16_dev", args.steps)):
+            if vp == prec:
+                continue
+            vsteps = max(2, vsteps)
+            hv = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=vp, **kw))
+            L.lbmhd_init(hv, *fields)
+            barrier()
+            t = max_over_ranks(timed_steps(L, hv, stream, vsteps, max(3, args.warmup // 10)))
+            L.lbmhd_destroy(hv)
+            vb = L.lbmhd_bytes_per_cell(vp)
+            variants[vp] = {
+                "MLUPS": world * cells * vsteps / t / 1e6, "steps": vsteps,
+                "bytes_per_cell": vb,
+                "hbm_frac": vb * cells * vsteps / t / 1e9 / hbm,
+            }
+
+    # ---- end to end through the host C ABI --------------------------------
+    e2e = None
+    if not args.no_e2e:
+        he = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
+        L.lbmhd_init(he, *fields)  # allocate/warm the path once
+        L.lbmhd_step(he, 3)
+        L.lbmhd_moments(he)
+        barrier()
+        t0 = time.perf_counter()
+        L.lbmhd_init(he, *fields)
+        L.lbmhd_step(he, args.steps)
+        out = L.lbmhd_moments(he)
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        L.lbmhd_destroy(he)
+        assert all(np.isfinite(a).all() for a in out)
+        e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 5 * 8 * cells / args.steps,
+               "d2h_bytes_per_step": 5 * 8 * cells / args.steps,
+               "job": f"lbmhd_init (5 host FP64 fields) + lbmhd_step({args.steps}) + "
+                      "lbmhd_moments (5 host FP64 fields); bytes amortised per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, s, cores, dtc = time_oracle(budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"512x512 lattice of the same recipe, {s} FP64 oracle steps "
+                         f"({dtc:.1f} s)"}
+
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as fh:
+                tj = json.load(fh).get(prec)
+            if tj and tj.get("valid"):
+                traffic = tj["bytes_per_cell"] * cells
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[prec].split(" ")[0], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": n, "ny": n, "precision": prec,
+                       "storage": DTYPES[prec],
+                       "l2": "state larger than L2 (%.1f GB per buffer), no flush"
+                             % (bpc / 2 * cells / 1e9),
+                       "parallelism": f"{world} independent lattice(s), one per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                         "bytes_per_cell": bpc},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(), "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=list(DTYPES), default="fp32")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

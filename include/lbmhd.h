@@ -1,0 +1,187 @@
+/*
+ * lbmhd.h -- C ABI of the GB300 (sm_103a) filtered lattice Boltzmann MHD
+ * library: a D2Q9 multi-relaxation-time density distribution and a D2Q5
+ * vector magnetic distribution on a periodic 2D lattice, with a local
+ * Smagorinsky-type eddy viscosity and eddy resistivity (Flint & Vahala,
+ * "Lattice Boltzmann Large Eddy Simulation Model of MHD", arXiv:1607.08675).
+ *
+ * Conventions shared by every entry point:
+ *  - All functions are extern "C"; those returning int return LBMHD_OK (0)
+ *    or a negative LBMHD_E* code and never abort.  lbmhd_last_error() gives
+ *    a message for the calling thread's last failure.
+ *  - A field is nx*ny doubles, node (x, y) at index y*nx + x (x fastest).
+ *  - Host pointers are owned by the caller and are not retained after the
+ *    call returns.  Device pointers (the *_device variants) must be
+ *    cudaMalloc'd (or torch) memory on the handle's device; they are read or
+ *    written in stream order on the handle's stream and not retained.
+ *  - The library owns all device memory of a handle; lbmhd_destroy frees it.
+ *  - After LBMHD_ECUDA a handle may only be destroyed.  After any other
+ *    error the handle is unchanged and stays usable.
+ *  - Calls on one handle must not race each other (one host thread at a
+ *    time); different handles are independent.
+ *
+ * Physics: streaming is the shift of Sec. 1.2 (pull form: f_i(x) <-
+ * f*_i(x - c_i)); the density collision relaxes the moments M = T f of
+ * Eq. FluidTMatrix towards Eq. KinMomentEq with diagonal rates s_j (Sec. 3);
+ * the magnetic collision is single-relaxation towards the D2Q5 equilibrium
+ * of Sec. 3 (Eq. LBMagEqn).  Transport coefficients follow Sec. 4.3:
+ * nu = (1/s_3 - 1/2)/3, eta = (1/s_m - 1/2)/3.  With les != 0 each node
+ * raises its relaxation times by the Smagorinsky increments
+ * nu_t = C_S Delta^2 |S| and eta_t = C_S Delta^2 |j| of
+ * Eqs. SmagorinskyMHDClosureV/B, with |S| and |j| taken from the node's own
+ * non-equilibrium moments (Sec. 1.2: sum c_a c_b f^(1) = -(rho tau/3) 2 S_ab)
+ * and the implicit dependence on tau solved exactly.
+ */
+#ifndef LBMHD_H
+#define LBMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMHD_ABI_VERSION 1u
+
+/* Status codes. */
+#define LBMHD_OK 0
+#define LBMHD_EINVAL (-1)     /* bad argument or parameter */
+#define LBMHD_ENOMEM (-2)     /* device or host allocation failed */
+#define LBMHD_ECUDA (-3)      /* CUDA runtime error; handle unusable */
+#define LBMHD_ENONFINITE (-4) /* a non-finite density was detected */
+#define LBMHD_ETIMEOUT (-5)   /* a bounded device wait expired */
+#define LBMHD_EVERSION (-6)   /* params.abi_version mismatch */
+#define LBMHD_ESTATE (-7)     /* call out of order (e.g. step before init) */
+
+/* Storage / arithmetic of a handle.  The populations are kept in HBM as
+ * 19 planes (9 f_i, then g_k x/y for k = 0..4).  *_DEV formats store the
+ * deviation from the rest equilibrium (f_i - w_i; g_k itself). */
+typedef enum {
+    LBMHD_FP64 = 0,     /* FP64 storage, FP64 arithmetic (parity mode) */
+    LBMHD_FP32 = 1,     /* FP32 storage of f and g, FP32 arithmetic */
+    LBMHD_FP32_DEV = 2, /* FP32 storage of deviations, FP32 arithmetic */
+    LBMHD_FP16_DEV = 3  /* FP16 storage of scaled deviations, FP32 arithmetic */
+} lbmhd_precision;
+
+typedef struct lbmhd_t lbmhd_t;
+
+/* Run parameters.  Fill with lbmhd_params_default, then override. */
+typedef struct {
+    uint32_t abi_version;  /* must be LBMHD_ABI_VERSION */
+    int32_t precision;     /* lbmhd_precision */
+    double tau_nu;         /* base 1/s_3 = 1/s_4, > 1/2 (Sec. 4.3: nu) */
+    double tau_eta;        /* base 1/s_m, > 1/2 (Sec. 4.3: eta) */
+    double C_S;            /* Smagorinsky constant, >= 0, enters linearly */
+    double delta;          /* filter width Delta in lattice units, > 0 */
+    double s5, s6;         /* energy-flux rates; <= 0: tied to 1/tau_nu */
+    double s7, s8;         /* energy rates; <= 0: tied to the local s_nu */
+    int32_t les;           /* 0: no eddy terms; 1: local Smagorinsky rates */
+    int32_t check_finite_every; /* 0: never; k: test rho every k steps */
+    double fp16_scale;     /* LBMHD_FP16_DEV: stored = deviation * scale */
+    void* stream;          /* cudaStream_t to run on; NULL: library stream */
+} lbmhd_params;
+
+/* FP64 diagnostics (sums over nodes in a fixed order, deterministic).
+ * <.> is the mean over nodes; omega, j_z and div B use periodic central
+ * differences of the node moments. */
+typedef struct {
+    double mass;           /* sum rho */
+    double mom_x, mom_y;   /* sum rho u */
+    double bsum_x, bsum_y; /* sum B */
+    double E_kin;          /* <rho |u|^2> / 2 */
+    double E_mag;          /* <|B|^2> / 2 */
+    double enstrophy;      /* <omega^2> / 2 */
+    double cross_helicity; /* <u . B> */
+    double divB_max;       /* max |div B| (Sec. 1.2 claim: div B = 0) */
+    double divB_rms;       /* sqrt <(div B)^2> */
+    double current_sq;     /* <j_z^2> / 2 */
+    int64_t step;          /* steps taken since init */
+} lbmhd_diag;
+
+/* Defaults: FP64, tau_nu = tau_eta = 0.6, C_S = 0.1, delta = 1, all of
+ * s5..s8 tied, les = 1, no finite check, fp16_scale = 1024, stream NULL. */
+void lbmhd_params_default(lbmhd_params* p);
+
+/* Validate p and allocate the two population buffers of an nx x ny
+ * periodic lattice on the current CUDA device.  Rejects (EINVAL) nx or
+ * ny < 1, tau <= 1/2, non-finite values, C_S < 0, delta <= 0, a given
+ * s5..s8 outside (0, 2), fp16_scale <= 0, and a non-positive bulk
+ * viscosity xi = -1/9 - 1/(9 s_4) - 1/(15 s_7) + 2/(5 s_8) (Sec. 4.3) at
+ * the base rates.  *out is set on success only. */
+int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out);
+
+/* Set the state to the local equilibria f^eq(rho, u, B), g^eq(u, B) of
+ * Sec. 3 (the paper gives no initial condition; equilibrium is taken).
+ * Arguments: five host fields (rho > 0).  Resets the step counter.
+ * Synchronises with the handle's stream before returning. */
+int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
+               const double* bx, const double* by);
+
+/* As lbmhd_init, from device fields; enqueued on the handle's stream. */
+int lbmhd_init_device(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
+                      const double* bx, const double* by);
+
+/* Advance n >= 0 time steps: each is one fused launch of pull-stream and
+ * collide (Sec. 1.2 and Sec. 3) over the whole lattice.  Asynchronous on
+ * the handle's stream; long runs replay a captured CUDA graph.  Returns
+ * ESTATE before init.  A pending non-finite report (check_finite_every)
+ * is returned by the next synchronising call. */
+int lbmhd_step(lbmhd_t* h, int n);
+
+/* rho, u and B of the current state (conserved by the collision, so they
+ * are the moments of Sec. 3 of the last streamed populations).  Host
+ * output fields; synchronises. */
+int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by);
+
+/* As lbmhd_moments, into device fields; enqueued, does not synchronise. */
+int lbmhd_moments_device(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx,
+                         double* by);
+
+/* FP64 diagnostics of the current state (see lbmhd_diag).  Synchronises. */
+int lbmhd_diagnostics(lbmhd_t* h, lbmhd_diag* out);
+
+/* Copy the 19 population planes out as FP64 (decoded from the storage
+ * format): host array of 19*nx*ny doubles, plane p at p*nx*ny.  Planes
+ * 0..8 are f_i in the order of the lattice lists of Sec. 3; plane 9+2k+a
+ * is component a of g_k.  Synchronises. */
+int lbmhd_get_state(lbmhd_t* h, double* state);
+
+/* Replace the state with host FP64 planes (layout as lbmhd_get_state),
+ * encoded to the storage format; the step counter is left unchanged.
+ * Together with lbmhd_get_state this is checkpoint / resume. */
+int lbmhd_set_state(lbmhd_t* h, const double* state);
+
+/* Wait for the handle's stream; reports a pending non-finite density. */
+int lbmhd_sync(lbmhd_t* h);
+
+/* Steps taken since the last init (host counter, no synchronisation). */
+int64_t lbmhd_step_count(const lbmhd_t* h);
+
+/* Algorithmic HBM bytes per node update of a step (19 populations read and
+ * 19 written): 304 (FP64), 152 (FP32, FP32_DEV), 76 (FP16_DEV); 0 for an
+ * unknown precision. */
+int lbmhd_bytes_per_cell(int precision);
+
+/* Number of step-kernel launches issued by this handle since creation. */
+int64_t lbmhd_launch_count(const lbmhd_t* h);
+
+/* Launch shape of the step kernel: vec nodes per thread along x (1, 2 or
+ * 4, dividing nx) and block threads per block (multiple of 32, <= 256).
+ * The default is the widest vector that divides nx (2 at most for FP64)
+ * and 256 threads.  Results do not depend on the shape.  EINVAL if the
+ * shape is not available. */
+int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
+int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
+
+/* Free everything the handle owns.  NULL is accepted. */
+void lbmhd_destroy(lbmhd_t* h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* lbmhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMHD_H */

@@ -1,0 +1,360 @@
+// lbmhd_aux.cu -- equilibrium initialisation, moments, state transfer,
+// the non-finite check and the FP64 diagnostics reduction.
+#include "lbmhd_device.cuh"
+#include "lbmhd_internal.h"
+
+namespace lbmhd {
+
+// ---- FP64 views of a stored value ---------------------------------------
+// abs: the population itself; dev: its deviation from the rest state.
+template <int P>
+__device__ __forceinline__ double dev_of(typename Fmt<P>::S v, int p, float inv_scale) {
+    if constexpr (P == P_FP64) return v - plane_rest<double>(p);
+    else if constexpr (P == P_FP32) return (double)v - (double)plane_rest<float>(p);
+    else if constexpr (P == P_FP32_DEV) return (double)v;
+    else return (double)__half2float(__ushort_as_half(v)) * (double)inv_scale;
+}
+// Rest value that dev_of subtracted (FP32 storage subtracts the FP32 weight).
+template <int P>
+__device__ __forceinline__ double rest_of(int p) {
+    if constexpr (P == P_FP32) return (double)plane_rest<float>(p);
+    else return plane_rest<double>(p);
+}
+template <int P>
+__device__ __forceinline__ typename Fmt<P>::S enc_d(double absval, double devval, float scale) {
+    if constexpr (P == P_FP64) return absval;
+    else if constexpr (P == P_FP32) return (float)absval;
+    else if constexpr (P == P_FP32_DEV) return (float)devval;
+    else return __half_as_ushort(__float2half_rn((float)(devval * (double)scale)));
+}
+
+// ---- equilibrium initialisation (Sec. 3 equilibria) ----------------------
+template <int P>
+__global__ void init_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
+                            const double* __restrict__ uy, const double* __restrict__ bx,
+                            const double* __restrict__ by, typename Fmt<P>::S* __restrict__ st,
+                            long long n, int nx, long long ps, float scale) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const long long y = c / nx, x = c - y * nx;
+        const long long o = y * nx + x;
+        const double r = rho[c], u = ux[c], v = uy[c], Bx = bx[c], By = by[c];
+        const double u2 = u * u + v * v, b2 = Bx * Bx + By * By;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double cx = plane_cx(i), cy = plane_cy(i);
+            const double cu = cx * u + cy * v, cb = cx * Bx + cy * By;
+            const double c2 = cx * cx + cy * cy, w = plane_rest<double>(i);
+            // f^eq - w = w (rho - 1) + w rho (3 cu + 9/2 cu^2 - 3/2 u^2)
+            //            + 9/2 w (B^2 c^2 / 2 - (B.c)^2)
+            const double kin = w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+            const double mag = 4.5 * w * (0.5 * b2 * c2 - cb * cb);
+            const double feq = w * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2) + mag;
+            const double dev = (w * (r - 1.0) + kin) + mag;
+            st[i * ps + o] = enc_d<P>(feq, dev, scale);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int p = 9 + 2 * k;
+            const double Cx = plane_cx(p), Cy = plane_cy(p);
+            const double wk = k == 0 ? 1.0 / 3.0 : 1.0 / 6.0;
+            const double Cu = Cx * u + Cy * v, CB = Cx * Bx + Cy * By;
+            const double gx = wk * (Bx + 3.0 * (Cu * Bx - CB * u));
+            const double gy = wk * (By + 3.0 * (Cu * By - CB * v));
+            st[p * ps + o] = enc_d<P>(gx, gx, scale);
+            st[(p + 1) * ps + o] = enc_d<P>(gy, gy, scale);
+        }
+    }
+}
+
+// ---- moments of a stored state ------------------------------------------
+template <int P>
+__device__ __forceinline__ void node_moments(const typename Fmt<P>::S* __restrict__ st,
+                                             long long ps, long long o, float inv_scale,
+                                             double& r, double& u, double& v, double& Bx,
+                                             double& By) {
+    double d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = dev_of<P>(st[i * ps + o], i, inv_scale);
+    double drho = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) drho += d[i];
+    const double jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const double jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    r = 1.0 + drho;  // the rest weights sum to one
+    u = jx / r;
+    v = jy / r;
+    Bx = 0.0;
+    By = 0.0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Bx += dev_of<P>(st[(9 + 2 * k) * ps + o], 9 + 2 * k, inv_scale);
+        By += dev_of<P>(st[(10 + 2 * k) * ps + o], 10 + 2 * k, inv_scale);
+    }
+}
+
+template <int P>
+__global__ void moments_kernel(const typename Fmt<P>::S* __restrict__ st, double* rho, double* ux,
+                               double* uy, double* bx, double* by, long long n, long long ps,
+                               float inv_scale) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        double r, u, v, Bx, By;
+        node_moments<P>(st, ps, c, inv_scale, r, u, v, Bx, By);
+        rho[c] = r;
+        ux[c] = u;
+        uy[c] = v;
+        bx[c] = Bx;
+        by[c] = By;
+    }
+}
+
+template <int P>
+__global__ void get_state_kernel(const typename Fmt<P>::S* __restrict__ st, double* out,
+                                 long long n, long long ps, float inv_scale) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const auto v = st[p * ps + c];
+            double a;
+            if constexpr (P == P_FP64) a = v;
+            else if constexpr (P == P_FP32) a = (double)v;
+            else a = rest_of<P>(p) + dev_of<P>(v, p, inv_scale);
+            out[p * n + c] = a;
+        }
+    }
+}
+
+template <int P>
+__global__ void set_state_kernel(const double* __restrict__ in, typename Fmt<P>::S* st,
+                                 long long n, long long ps, float scale) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const double a = in[p * n + c];
+            st[p * ps + c] = enc_d<P>(a, a - plane_rest<double>(p), scale);
+        }
+    }
+}
+
+template <int P>
+__global__ void finite_kernel(const typename Fmt<P>::S* __restrict__ st, int* flag, long long n,
+                              long long ps, float inv_scale) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double a = dev_of<P>(st[c], 0, inv_scale);
+        const double b = dev_of<P>(st[9 * ps + c], 9, inv_scale);
+        if (!isfinite(a) || !isfinite(b)) atomicExch(flag, 1);
+    }
+}
+
+// ---- diagnostics ----------------------------------------------------------
+// Each block walks tiles of 32 x 8 nodes in a fixed order.  A tile's node
+// moments (and a one-node periodic halo) are staged in shared memory, so
+// the central differences of omega, j_z and div B read neighbours from
+// there.  Per-thread FP64 accumulators -> fixed warp-shuffle tree -> fixed
+// cross-warp order -> one partial row per block; a single-block pass then
+// combines the rows in block order.  Same lattice, same result, bit for bit.
+constexpr int kTX = 32, kTY = 8, kDiagBlocks = 1024, kNQ = 12;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTX* kTY) diag_kernel(const typename Fmt<P>::S* __restrict__ st,
+                                                         int nx, int ny, long long ps,
+                                                         float inv_scale, double* partials) {
+    __shared__ double sr[kTY + 2][kTX + 2], su[kTY + 2][kTX + 2], sv[kTY + 2][kTX + 2],
+        sbx[kTY + 2][kTX + 2], sby[kTY + 2][kTX + 2];
+    __shared__ double red[kTX * kTY / 32][kNQ];
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int tiles_x = (nx + kTX - 1) / kTX, tiles_y = (ny + kTY - 1) / kTY;
+    const int ntiles = tiles_x * tiles_y;
+    double acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+        __syncthreads();
+        for (int h = threadIdx.x; h < (kTX + 2) * (kTY + 2); h += blockDim.x) {
+            const int hx = h % (kTX + 2), hy = h / (kTX + 2);
+            int gx = (x0 + hx - 1) % nx, gy = (y0 + hy - 1) % ny;
+            if (gx < 0) gx += nx;
+            if (gy < 0) gy += ny;
+            double r, u, v, Bx, By;
+            node_moments<P>(st, ps, (long long)gy * nx + gx, inv_scale, r, u, v, Bx, By);
+            sr[hy][hx] = r;
+            su[hy][hx] = u;
+            sv[hy][hx] = v;
+            sbx[hy][hx] = Bx;
+            sby[hy][hx] = By;
+        }
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < nx && y < ny) {
+            const int hx = tx + 1, hy = ty + 1;
+            const double r = sr[hy][hx], u = su[hy][hx], v = sv[hy][hx];
+            const double Bx = sbx[hy][hx], By = sby[hy][hx];
+            acc[0] += r;
+            acc[1] += r * u;
+            acc[2] += r * v;
+            acc[3] += Bx;
+            acc[4] += By;
+            acc[5] += r * (u * u + v * v);
+            acc[6] += Bx * Bx + By * By;
+            const double om = 0.5 * (sv[hy][hx + 1] - sv[hy][hx - 1]) -
+                              0.5 * (su[hy + 1][hx] - su[hy - 1][hx]);
+            acc[7] += om * om;
+            acc[8] += u * Bx + v * By;
+            const double dv = 0.5 * (sbx[hy][hx + 1] - sbx[hy][hx - 1]) +
+                              0.5 * (sby[hy + 1][hx] - sby[hy - 1][hx]);
+            acc[9] = fmax(acc[9], fabs(dv));
+            acc[10] += dv * dv;
+            const double jz = 0.5 * (sby[hy][hx + 1] - sby[hy][hx - 1]) -
+                              0.5 * (sbx[hy + 1][hx] - sbx[hy - 1][hx]);
+            acc[11] += jz * jz;
+        }
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) {
+        const double w = q == 9 ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if (lane == 0) red[warp][q] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNQ) {
+        const int q = threadIdx.x;
+        double s = red[0][q];
+        for (int w = 1; w < kTX * kTY / 32; ++w) s = q == 9 ? fmax(s, red[w][q]) : s + red[w][q];
+        partials[(long long)blockIdx.x * kNQ + q] = s;
+    }
+}
+
+__global__ void diag_final_kernel(const double* __restrict__ partials, int nblocks, double ncell,
+                                  double* out) {
+    __shared__ double red[256 / 32][kNQ];
+    double acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q)
+            acc[q] = q == 9 ? fmax(acc[q], partials[b * kNQ + q]) : acc[q] + partials[b * kNQ + q];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) {
+        const double w = q == 9 ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if (lane == 0) red[warp][q] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[kNQ];
+        for (int q = 0; q < kNQ; ++q) {
+            s[q] = red[0][q];
+            for (int w = 1; w < 256 / 32; ++w) s[q] = q == 9 ? fmax(s[q], red[w][q]) : s[q] + red[w][q];
+        }
+        const double inv = 1.0 / ncell;
+        out[0] = s[0];
+        out[1] = s[1];
+        out[2] = s[2];
+        out[3] = s[3];
+        out[4] = s[4];
+        out[5] = 0.5 * s[5] * inv;
+        out[6] = 0.5 * s[6] * inv;
+        out[7] = 0.5 * s[7] * inv;
+        out[8] = s[8] * inv;
+        out[9] = s[9];
+        out[10] = sqrt(s[10] * inv);
+        out[11] = 0.5 * s[11] * inv;
+    }
+}
+
+// ---- launchers ------------------------------------------------------------
+static unsigned grid_for(long long n, int block) {
+    long long b = (n + block - 1) / block;
+    if (b > 65535LL * 8) b = 65535LL * 8;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+#define LBMHD_DISPATCH(prec, CALL)            \
+    switch (prec) {                           \
+        case P_FP64: { constexpr int P = P_FP64; CALL; } break;         \
+        case P_FP32: { constexpr int P = P_FP32; CALL; } break;         \
+        case P_FP32_DEV: { constexpr int P = P_FP32_DEV; CALL; } break; \
+        case P_FP16_DEV: { constexpr int P = P_FP16_DEV; CALL; } break; \
+        default: return cudaErrorInvalidValue;                          \
+    }
+
+cudaError_t launch_init(int prec, const double* rho, const double* ux, const double* uy,
+                        const double* bx, const double* by, void* state, const Geom& g,
+                        const HostColl& c, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    LBMHD_DISPATCH(prec, (init_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
+                             rho, ux, uy, bx, by, (typename Fmt<P>::S*)state, n, g.nx, g.ps,
+                             c.scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int prec, const void* state, double* rho, double* ux, double* uy,
+                           double* bx, double* by, const Geom& g, const HostColl& c,
+                           cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    LBMHD_DISPATCH(prec, (moments_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
+                             (const typename Fmt<P>::S*)state, rho, ux, uy, bx, by, n, g.ps,
+                             c.inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(int prec, const void* state, double* out, const Geom& g,
+                             const HostColl& c, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    LBMHD_DISPATCH(prec, (get_state_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
+                             (const typename Fmt<P>::S*)state, out, n, g.ps, c.inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(int prec, const double* in, void* state, const Geom& g,
+                             const HostColl& c, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    LBMHD_DISPATCH(prec, (set_state_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
+                             in, (typename Fmt<P>::S*)state, n, g.ps, c.scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Geom& g,
+                                const HostColl& c, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny;
+    LBMHD_DISPATCH(prec, (finite_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
+                             (const typename Fmt<P>::S*)state, flag, n, g.ps, c.inv_scale)));
+    return cudaGetLastError();
+}
+
+int diag_num_blocks(const Geom& g) {
+    const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
+    return (int)(tiles < kDiagBlocks ? tiles : kDiagBlocks);
+}
+
+cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
+                        const Geom& g, const HostColl& c, cudaStream_t st) {
+    const int nb = diag_num_blocks(g);
+    LBMHD_DISPATCH(prec, (diag_kernel<P><<<nb, kTX * kTY, 0, st>>>(
+                             (const typename Fmt<P>::S*)state, g.nx, g.ny, g.ps, c.inv_scale,
+                             partials)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, 256, 0, st>>>(partials, nb, (double)g.nx * g.ny, out12);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmhd

@@ -1,0 +1,167 @@
+// lbmhd_device.cuh -- device-side arithmetic of the filtered LB-MHD step
+// (Flint & Vahala, arXiv:1607.08675): storage formats, the per-node MRT +
+// local-LES collision of the D2Q9 density populations and the SRT
+// collision of the D2Q5 vector magnetic populations, all in registers.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbmhd {
+
+constexpr int kPlanes = 19;  // 9 f_i, then g_k (x, y) for k = 0..4
+
+// Lattice (Sec. 3, explicit lists): c_x, c_y of the D2Q9 set and C_x, C_y
+// of the D2Q5 set, expanded to the 19 storage planes.  Streaming pulls
+// plane p at node x from x - c_p.
+__host__ __device__ constexpr int plane_cx(int p) {
+    return p < 9 ? (p == 1 || p == 5 || p == 8 ? 1 : (p == 3 || p == 6 || p == 7 ? -1 : 0))
+                 : ((p - 9) / 2 == 1 ? 1 : ((p - 9) / 2 == 3 ? -1 : 0));
+}
+__host__ __device__ constexpr int plane_cy(int p) {
+    return p < 9 ? (p == 2 || p == 5 || p == 6 ? 1 : (p == 4 || p == 7 || p == 8 ? -1 : 0))
+                 : ((p - 9) / 2 == 2 ? 1 : ((p - 9) / 2 == 4 ? -1 : 0));
+}
+// Rest-state equilibrium (rho = 1, u = B = 0) of each plane: the D2Q9
+// weights w_i = 4/9, 1/9, 1/36 (fixed by Eq. KinMomentEq); g has none.
+template <class R>
+__host__ __device__ constexpr R plane_rest(int p) {
+    return p == 0 ? R(4) / R(9) : (p < 5 ? R(1) / R(9) : (p < 9 ? R(1) / R(36) : R(0)));
+}
+
+// Storage formats.  Every format is decoded to the deviation d = f - w
+// (and g itself) in the arithmetic type R, and encoded back from it.
+enum Prec { P_FP64 = 0, P_FP32 = 1, P_FP32_DEV = 2, P_FP16_DEV = 3 };
+
+template <int P> struct Fmt;
+template <> struct Fmt<P_FP64> {
+    using S = double;
+    using R = double;
+    static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest<R>(p); }
+};
+template <> struct Fmt<P_FP32> {
+    using S = float;
+    using R = float;
+    static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest<R>(p); }
+};
+template <> struct Fmt<P_FP32_DEV> {
+    using S = float;
+    using R = float;
+    static __device__ __forceinline__ R dec(S v, int, float) { return v; }
+    static __device__ __forceinline__ S enc(R d, int, float) { return d; }
+};
+template <> struct Fmt<P_FP16_DEV> {
+    using S = unsigned short;  // raw binary16 bits
+    using R = float;
+    // stored = d * scale; decoded with the exact reciprocal (power of two)
+    static __device__ __forceinline__ R dec(S v, int, float inv_scale) {
+        return __half2float(__ushort_as_half(v)) * inv_scale;
+    }
+    static __device__ __forceinline__ S enc(R d, int, float scale) {
+        return __half_as_ushort(__float2half_rn(d * scale));
+    }
+};
+
+// Collision parameters in the arithmetic type.
+template <class R>
+struct Coll {
+    R tn, te;        // base tau_nu, tau_eta
+    R tn2, te2;      // their squares
+    R k18, k36;      // 18 C_S Delta^2, 36 C_S Delta^2
+    R s5, s6;        // resolved energy-flux rates
+    R s7, s8;        // fixed rates (used when > 0), else tied to s_nu
+    int les;
+};
+
+// One node: d[9] = streamed f_i - w_i, g[10] = streamed g_k (x, y);
+// overwritten with the post-collision values.
+//
+// Density (Sec. 3): moments M_j = T_j . f for j = 3..8 (Eq. FluidTMatrix
+// rows; the rest state contributes only to M_8, by 5/3), equilibria of
+// Eq. KinMomentEq, n_j = M_j - M_j^eq.  Local eddy rate: Q = sqrt(n_4^2 +
+// 4 n_3^2) gives |S| = 3 Q / (2 rho tau); tau_e = tau_nu + 3 C_S Delta^2 |S|
+// solved as tau_e = (tau_nu + sqrt(tau_nu^2 + 18 C_S Delta^2 Q / rho)) / 2.
+// Relaxation M_j <- M_j - s_j n_j and return through T^-1 = T^t diag(1/|T_j|^2)
+// (the rows of T are orthogonal), i.e. f_i <- f_i - sum_j s_j n_j T_ji / |T_j|^2.
+//
+// Magnetic (Sec. 3, Eq. LBMagEqn): B = sum g_k, D2Q5 equilibrium
+// g_k^eq = w'_k [B + 3((C_k.u) B - (C_k.B) u)], which with E = u_x B_y -
+// u_y B_x is B/3 at rest and (B +- 3E e_perp)/6 on the axes.  The
+// antisymmetric non-equilibrium first moment (N_y1 - N_x2)^neq =
+// -(tau_m/3) j_z gives |j|; tau_m = (tau_eta + sqrt(tau_eta^2 +
+// 36 C_S Delta^2 J)) / 2 with J = |N_y1 - N_x2 - 2E|.  g <- g - (g - g^eq)/tau_m.
+template <class R>
+__device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c) {
+    const R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R rho = R(1) + drho;
+    const R irho = R(1) / rho;
+    const R ux = jx * irho, uy = jy * irho;
+    const R bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
+    const R by = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
+
+    const R dsum = (d[5] + d[6]) + (d[7] + d[8]);
+    const R m3 = (d[5] - d[6]) + (d[7] - d[8]);
+    const R m4 = (d[1] + d[3]) - (d[2] + d[4]);
+    const R m5 = R(2) * (d[3] - d[1]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const R m6 = R(2) * (d[4] - d[2]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R m7 = R(4) * d[0] - R(5) * ((d[1] + d[2]) + (d[3] + d[4])) + R(4) * dsum;
+    const R m8 = R(4) * d[0] - dsum;
+
+    const R j2i = (jx * jx + jy * jy) * irho;
+    const R n3 = m3 - (jx * jy * irho - bx * by);
+    const R n4 = m4 - ((jx * jx - jy * jy) * irho - bx * bx + by * by);
+    const R n5 = m5 + jx;
+    const R n6 = m6 + jy;
+    const R n7 = m7 + R(3) * j2i;
+    const R n8 = m8 - (R(5) / R(3) * drho - R(3) * j2i);
+
+    // Ny1 = sum_k C_kx g_ky, Nx2 = sum_k C_ky g_kx; Ny1^eq = E = -Nx2^eq
+    const R E = ux * by - uy * bx;
+    R tau_e = c.tn, tau_m = c.te;
+    if (c.les) {
+        const R Q = sqrt(n4 * n4 + R(4) * (n3 * n3));
+        tau_e = R(0.5) * (c.tn + sqrt(c.tn2 + c.k18 * Q * irho));
+        const R Ny1 = g[3] - g[7];
+        const R Nx2 = g[4] - g[8];
+        const R J = fabs(Ny1 - Nx2 - R(2) * E);
+        tau_m = R(0.5) * (c.te + sqrt(c.te2 + c.k36 * J));
+    }
+    const R snu = R(1) / tau_e;
+    const R s7 = c.s7 > R(0) ? c.s7 : snu;
+    const R s8 = c.s8 > R(0) ? c.s8 : snu;
+
+    const R a3 = snu * n3 * R(0.25);
+    const R a4 = snu * n4 * R(0.25);
+    const R a5 = c.s5 * n5 * (R(1) / R(12));
+    const R a6 = c.s6 * n6 * (R(1) / R(12));
+    const R a7 = s7 * n7 * (R(1) / R(180));
+    const R a8 = s8 * n8 * (R(1) / R(20));
+
+    const R q78 = R(4) * a7 - a8;
+    d[0] -= R(4) * (a7 + a8);
+    d[1] -= a4 - R(2) * a5 - R(5) * a7;
+    d[2] -= -a4 - R(2) * a6 - R(5) * a7;
+    d[3] -= a4 + R(2) * a5 - R(5) * a7;
+    d[4] -= -a4 + R(2) * a6 - R(5) * a7;
+    d[5] -= (a3 + a5) + (a6 + q78);
+    d[6] -= (a6 - a3) - (a5 - q78);
+    d[7] -= (a3 - a5) - (a6 - q78);
+    d[8] -= (a5 - a3) - (a6 - q78);
+
+    const R sm = R(1) / tau_m;
+    const R third = R(1) / R(3), sixth = R(1) / R(6);
+    const R e3 = R(3) * E;
+    const R geq[10] = {third * bx,        third * by,          // k = 0
+                       sixth * bx,        sixth * (by + e3),   // k = 1 (+x)
+                       sixth * (bx - e3), sixth * by,          // k = 2 (+y)
+                       sixth * bx,        sixth * (by - e3),   // k = 3 (-x)
+                       sixth * (bx + e3), sixth * by};         // k = 4 (-y)
+#pragma unroll
+    for (int q = 0; q < 10; ++q) g[q] -= sm * (g[q] - geq[q]);
+}
+
+}  // namespace lbmhd

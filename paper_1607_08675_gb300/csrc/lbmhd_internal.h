@@ -1,0 +1,88 @@
+// lbmhd_internal.h -- declarations shared by the library's translation
+// units (kernel launchers and the handle).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbmhd.h"
+
+namespace lbmhd {
+
+constexpr int kNumPlanes = 19;  // 9 f_i, then g_k (x, y) for k = 0..4
+
+// Host-side copy of the collision parameters; converted to the arithmetic
+// type of a precision by the launchers.
+struct HostColl {
+    double tn, te, k18, k36, s5, s6, s7, s8;
+    int les;
+    float scale, inv_scale;  // FP16_DEV encoding
+};
+
+// Geometry of one lattice in device memory: 19 planes of ps elements each,
+// node (x, y) at y*nx + x within a plane.
+struct Geom {
+    int nx, ny;
+    long long ps;  // plane stride in elements (padded)
+};
+
+size_t storage_bytes(int prec);   // bytes of one stored value
+long long plane_stride(int nx, int ny);
+
+// Fused stream-collide step: src -> dst (both 19 planes).  vec = nodes per
+// thread along x (1, 2, 4; nx % vec == 0), block = threads per block,
+// max_blocks = 0 for an exact cover, else a grid-stride cap.
+cudaError_t launch_step(int prec, int vec, int block, int max_blocks, const void* src, void* dst,
+                        const Geom& g, const HostColl& c, cudaStream_t st);
+bool step_variant_ok(int prec, int vec, int nx);
+
+// Equilibrium initialisation from five FP64 device fields.
+cudaError_t launch_init(int prec, const double* rho, const double* ux, const double* uy,
+                        const double* bx, const double* by, void* state, const Geom& g,
+                        const HostColl& c, cudaStream_t st);
+// Moments of a stored state into five FP64 device fields.
+cudaError_t launch_moments(int prec, const void* state, double* rho, double* ux, double* uy,
+                           double* bx, double* by, const Geom& g, const HostColl& c,
+                           cudaStream_t st);
+// Decode to / encode from 19 FP64 planes of nx*ny (unpadded).
+cudaError_t launch_get_state(int prec, const void* state, double* out, const Geom& g,
+                             const HostColl& c, cudaStream_t st);
+cudaError_t launch_set_state(int prec, const double* in, void* state, const Geom& g,
+                             const HostColl& c, cudaStream_t st);
+// Sets *flag to 1 if the density or the magnetic rest population is not
+// finite anywhere.
+cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Geom& g,
+                                const HostColl& c, cudaStream_t st);
+
+// Diagnostics: per-block FP64 partials then one fixed-order final pass.
+int diag_num_blocks(const Geom& g);
+cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
+                        const Geom& g, const HostColl& c, cudaStream_t st);
+
+void set_error(const std::string& msg);
+
+}  // namespace lbmhd
+
+struct lbmhd_t {
+    lbmhd::Geom geom;
+    lbmhd_params p;
+    lbmhd::HostColl coll;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    bool capturable;
+    void* buf[2];
+    int cur;
+    bool initialised;
+    bool failed;
+    int64_t steps;
+    int64_t launches;
+    double* d_partials;
+    double* d_diag;
+    int* d_flag;
+    int vec, block;
+    cudaGraphExec_t graph;
+    int graph_steps;
+};

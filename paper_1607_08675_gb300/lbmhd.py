@@ -1,0 +1,260 @@
+"""Thin ctypes binding of ``liblbmhd.so`` (C ABI: include/lbmhd.h).
+
+Every function here only marshals arguments: the lattice step, the
+moments, the diagnostics and the state transfers all run in the CUDA
+library.  The names follow the C ABI.  If the library has not been built
+the first call raises; there is no fallback.
+
+Fields are float64 numpy arrays of shape (ny, nx) (x fastest); device
+fields are contiguous float64 CUDA torch tensors of the same shape.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbmhd.so")
+
+ABI_VERSION = 1
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_dev": 2, "fp16_dev": 3}
+ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
+          -6: "EVERSION", -7: "ESTATE"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("abi_version", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("tau_nu", ctypes.c_double), ("tau_eta", ctypes.c_double),
+                ("C_S", ctypes.c_double), ("delta", ctypes.c_double),
+                ("s5", ctypes.c_double), ("s6", ctypes.c_double),
+                ("s7", ctypes.c_double), ("s8", ctypes.c_double),
+                ("les", ctypes.c_int32), ("check_finite_every", ctypes.c_int32),
+                ("fp16_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+DIAG_KEYS = ("mass", "mom_x", "mom_y", "bsum_x", "bsum_y", "E_kin", "E_mag", "enstrophy",
+             "cross_helicity", "divB_max", "divB_rms", "current_sq")
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in DIAG_KEYS] + [("step", ctypes.c_int64)]
+
+
+class LBMHDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it was never built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            h, i, d, vp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            sig = {
+                "lbmhd_params_default": (None, [ctypes.POINTER(Params)]),
+                "lbmhd_create": (i, [i, i, ctypes.POINTER(Params), pp]),
+                "lbmhd_init": (i, [h, vp, vp, vp, vp, vp]),
+                "lbmhd_init_device": (i, [h, vp, vp, vp, vp, vp]),
+                "lbmhd_step": (i, [h, i]),
+                "lbmhd_moments": (i, [h, vp, vp, vp, vp, vp]),
+                "lbmhd_moments_device": (i, [h, vp, vp, vp, vp, vp]),
+                "lbmhd_diagnostics": (i, [h, ctypes.POINTER(Diag)]),
+                "lbmhd_get_state": (i, [h, vp]),
+                "lbmhd_set_state": (i, [h, vp]),
+                "lbmhd_sync": (i, [h]),
+                "lbmhd_step_count": (ctypes.c_int64, [h]),
+                "lbmhd_launch_count": (ctypes.c_int64, [h]),
+                "lbmhd_bytes_per_cell": (i, [i]),
+                "lbmhd_set_launch": (i, [h, i, i]),
+                "lbmhd_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i)]),
+                "lbmhd_destroy": (None, [h]),
+                "lbmhd_last_error": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LBMHDError(rc, lib().lbmhd_last_error().decode())
+
+
+def _host(a: np.ndarray, shape) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _dev(t, shape):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and tuple(t.shape) == shape):
+        raise ValueError(f"expected a contiguous float64 CUDA tensor of shape {shape}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lbmhd_params_default(**overrides) -> Params:
+    """Default parameters (lbmhd_params_default) with keyword overrides;
+    ``precision`` may be a name from PRECISIONS, ``stream`` an int handle
+    or a torch.cuda.Stream."""
+    p = Params()
+    lib().lbmhd_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """An lbmhd_t* together with its lattice shape."""
+
+    def __init__(self, ptr: int, nx: int, ny: int, params: Params):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.nx, self.ny = nx, ny
+        self.params = params
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+
+def lbmhd_create(nx: int, ny: int, params: Params | None = None) -> Handle:
+    params = params if params is not None else lbmhd_params_default()
+    out = ctypes.c_void_p()
+    _check(lib().lbmhd_create(int(nx), int(ny), ctypes.byref(params), ctypes.byref(out)))
+    return Handle(out.value, nx, ny, params)
+
+
+def lbmhd_init(h: Handle, rho, ux, uy, bx, by):
+    arrs = [_host(a, h.shape) for a in (rho, ux, uy, bx, by)]
+    _check(lib().lbmhd_init(h.ptr, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs]))
+
+
+def lbmhd_init_device(h: Handle, rho, ux, uy, bx, by):
+    _check(lib().lbmhd_init_device(h.ptr, *[_dev(t, h.shape) for t in (rho, ux, uy, bx, by)]))
+
+
+def lbmhd_step(h: Handle, n: int = 1):
+    _check(lib().lbmhd_step(h.ptr, int(n)))
+
+
+def lbmhd_moments(h: Handle):
+    out = [np.empty(h.shape) for _ in range(5)]
+    _check(lib().lbmhd_moments(h.ptr, *[a.ctypes.data_as(ctypes.c_void_p) for a in out]))
+    return tuple(out)
+
+
+def lbmhd_moments_device(h: Handle, rho, ux, uy, bx, by):
+    _check(lib().lbmhd_moments_device(h.ptr, *[_dev(t, h.shape) for t in (rho, ux, uy, bx, by)]))
+
+
+def lbmhd_diagnostics(h: Handle) -> dict:
+    d = Diag()
+    _check(lib().lbmhd_diagnostics(h.ptr, ctypes.byref(d)))
+    out = {k: getattr(d, k) for k in DIAG_KEYS}
+    out["step"] = d.step
+    return out
+
+
+def lbmhd_get_state(h: Handle) -> np.ndarray:
+    st = np.empty((19,) + h.shape)
+    _check(lib().lbmhd_get_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
+    return st
+
+
+def lbmhd_set_state(h: Handle, state):
+    st = _host(state, (19,) + h.shape)
+    _check(lib().lbmhd_set_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
+
+
+def lbmhd_sync(h: Handle):
+    _check(lib().lbmhd_sync(h.ptr))
+
+
+def lbmhd_step_count(h: Handle) -> int:
+    return int(lib().lbmhd_step_count(h.ptr))
+
+
+def lbmhd_launch_count(h: Handle) -> int:
+    return int(lib().lbmhd_launch_count(h.ptr))
+
+
+def lbmhd_bytes_per_cell(precision) -> int:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return int(lib().lbmhd_bytes_per_cell(int(precision)))
+
+
+def lbmhd_set_launch(h: Handle, vec: int, block: int):
+    _check(lib().lbmhd_set_launch(h.ptr, int(vec), int(block)))
+
+
+def lbmhd_get_launch(h: Handle):
+    v, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbmhd_get_launch(h.ptr, ctypes.byref(v), ctypes.byref(b)))
+    return v.value, b.value
+
+
+def lbmhd_destroy(h: Handle):
+    if h is not None and h.ptr:
+        lib().lbmhd_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+
+
+class Lattice:
+    """Convenience owner of one handle (context manager)."""
+
+    def __init__(self, nx: int, ny: int, **params):
+        self.h = lbmhd_create(nx, ny, lbmhd_params_default(**params))
+
+    def init(self, rho, ux, uy, bx, by):
+        lbmhd_init(self.h, rho, ux, uy, bx, by)
+        return self
+
+    def step(self, n: int = 1):
+        lbmhd_step(self.h, n)
+        return self
+
+    def moments(self):
+        return lbmhd_moments(self.h)
+
+    def diagnostics(self):
+        return lbmhd_diagnostics(self.h)
+
+    def state(self):
+        return lbmhd_get_state(self.h)
+
+    def set_state(self, st):
+        lbmhd_set_state(self.h, st)
+
+    def close(self):
+        lbmhd_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
