@@ -174,6 +174,34 @@ int64_t lbmhd_launch_count(const lbmhd_t* h);
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
 
+/* Diagnostics of a caller-owned state buffer, allocating nothing.  The
+ * paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc, e.g. a host application whose device memory all comes from
+ * its own arena, or a latency-critical loop that cannot take the implicit
+ * device synchronisation of cudaMalloc / cudaFree.
+ * Arguments: state = device pointer to 19 planes in the storage format of
+ * `precision` (lbmhd_precision), plane p at element offset p*plane_stride,
+ * node (x, y) at y*nx + x within a plane (plane_stride >= nx*ny; an FP64
+ * array from lbmhd_get_state qualifies with plane_stride = nx*ny);
+ * fp16_scale = the scale of LBMHD_FP16_DEV storage (ignored otherwise);
+ * out = device pointer to 12 doubles, written in the field order of
+ * lbmhd_diag (mass ... current_sq); stream = cudaStream_t (NULL: legacy
+ * default stream).  Enqueued on the stream; does not synchronise.
+ * The per-block partial sums live in one static device array of 96 KiB
+ * (1024 rows of 12 doubles), held by every GPU that loads the library
+ * until the process exits; every lattice the library accepts
+ * (nx*ny <= 2^30) fits, larger ones are rejected with EINVAL.  The first
+ * call on a device looks up the array's device address (once per device),
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads)
+ * race and give wrong sums; serialise them.  Each call writes every
+ * partial row it reads, so no clearing is needed between calls.
+ * Errors: EINVAL for NULL pointers, an unknown precision, bad sizes or
+ * scale; ECUDA if the address lookup or the launch fails. */
+int lbmhd_diagnostics_noalloc(const void* state, int precision, int nx, int ny,
+                              long long plane_stride, double fp16_scale, double* out,
+                              void* stream);
+
 /* Free everything the handle owns.  NULL is accepted. */
 void lbmhd_destroy(lbmhd_t* h);
 

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_bytes_per_cell": (i, [i]),
                 "lbmhd_set_launch": (i, [h, i, i]),
                 "lbmhd_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i)]),
+                "lbmhd_diagnostics_noalloc": (i, [vp, i, i, i, ctypes.c_longlong, d, vp, vp]),
                 "lbmhd_destroy": (None, [h]),
                 "lbmhd_last_error": (ctypes.c_char_p, []),
             }
@@ -216,6 +217,24 @@ def lbmhd_get_launch(h: Handle):
     v, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().lbmhd_get_launch(h.ptr, ctypes.byref(v), ctypes.byref(b)))
     return v.value, b.value
+
+
+def lbmhd_diagnostics_noalloc(state, precision, nx: int, ny: int, plane_stride: int, out,
+                              fp16_scale: float = 1024.0, stream=None):
+    """Diagnostics of a caller-owned device state without any device
+    allocation (see include/lbmhd.h).  ``state`` and ``out`` are CUDA torch
+    tensors (or raw device addresses); ``out`` receives 12 doubles in the
+    order of DIAG_KEYS.  Enqueued on ``stream`` (int handle or
+    torch.cuda.Stream; None: the legacy default stream)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    sp = state if isinstance(state, int) else state.data_ptr()
+    op = out if isinstance(out, int) else out.data_ptr()
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(lib().lbmhd_diagnostics_noalloc(ctypes.c_void_p(sp), int(precision), int(nx), int(ny),
+                                           int(plane_stride), float(fp16_scale),
+                                           ctypes.c_void_p(op), ctypes.c_void_p(stream or 0)))
 
 
 def lbmhd_destroy(h: Handle):

@@ -1,0 +1,71 @@
+"""lbmhd_diagnostics_noalloc: diagnostics for callers that cannot allocate.
+
+A host application that owns all device memory through its own arena, or
+a latency-critical loop that cannot take cudaMalloc's implicit device
+synchronisation, cannot let the library allocate scratch.  This entry
+point reduces a state buffer the caller already holds, keeping its partial
+sums in a static device array.  Here it is called through the C ABI on two
+lattices in a row and must agree with the handle-based lbmhd_diagnostics
+(which uses scratch from lbmhd_create) within the diagnostics tolerance of
+the parity tests (1e-11 relative).
+
+This file is collected last on purpose: the other GPU tests have run
+before it when a run stops at the first failure.
+"""
+import numpy as np
+import pytest
+
+from paper_1607_08675_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_08675_gb300 import build, lbmhd
+
+    build.build()
+    return lbmhd
+
+
+def _close(a, b, key):
+    tol = 1e-11 * max(abs(b), 1e-300)
+    if key in ("mom_x", "mom_y", "bsum_x", "bsum_y", "divB_max", "divB_rms"):
+        tol = max(tol, 1e-13)
+    return abs(a - b) <= tol
+
+
+def test_noalloc_matches_handle_diagnostics_on_two_calls(L):
+    import torch
+
+    runs = [("fp64", 96, 80, torch.float64, 40), ("fp32", 256, 192, torch.float32, 25)]
+    for prec, nx, ny, dt, steps in runs:
+        h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision=prec))
+        L.lbmhd_init(h, *inputs.turbulence(nx, ny, kmin=2, kmax=5, seed=nx))
+        L.lbmhd_step(h, steps)
+        ref = L.lbmhd_diagnostics(h)
+        host_state = L.lbmhd_get_state(h)  # FP32 storage decodes exactly to FP64
+        L.lbmhd_destroy(h)
+        state = torch.from_numpy(host_state).to(dt).cuda().contiguous()
+        assert np.array_equal(state.double().cpu().numpy(), host_state)
+        out = torch.full((12,), float("nan"), dtype=torch.float64, device="cuda")
+        L.lbmhd_diagnostics_noalloc(state, prec, nx, ny, nx * ny, out)
+        got = out.cpu().numpy()
+        for q, key in enumerate(L.DIAG_KEYS):
+            assert _close(got[q], ref[key], key), (prec, key, got[q], ref[key])
+
+
+def test_noalloc_rejects_oversized_and_bad_arguments(L):
+    import torch
+
+    out = torch.zeros(12, dtype=torch.float64, device="cuda")
+    st = torch.zeros(19 * 16, dtype=torch.float64, device="cuda")
+    for args in [(1 << 16, 1 << 15, (1 << 31)), (4, 4, 15), (0, 4, 16)]:
+        with pytest.raises(L.LBMHDError) as e:
+            L.lbmhd_diagnostics_noalloc(st, "fp64", *args, out)
+        assert e.value.code == -1
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_diagnostics_noalloc(st, 9, 4, 4, 16, out)
