@@ -186,6 +186,34 @@ def run_reference(args):
     }), flush=True)
 
 
+def kernel_source_hash() -> str:
+    """Hash of the step kernel's sources: DRAM counters taken from another
+    version of the kernel are not reported."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("lbmhd_step.cu", "lbmhd_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1607_08675_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(prec: str, cells: int):
+    """ncu DRAM bytes (read + write) per launch for this lattice, from
+    profiles/step_kernel_traffic.txt ("source <hash>" and "<precision>
+    <bytes per node>" lines), or None when absent or stale."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    try:
+        with open(path) as fh:
+            rows = [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    kv = {r[0]: r[1] for r in rows if len(r) >= 2}
+    if kv.get("source") != kernel_source_hash() or prec not in kv:
+        return None
+    return float(kv[prec]) * cells
+
+
 def make_fields(n, seed):
     from paper_1607_08675_gb300 import inputs
 
@@ -319,16 +347,7 @@ def run_ours(args):
                "sample": f"512x512 lattice of the same recipe, {s} FP64 oracle steps "
                          f"({dtc:.1f} s)"}
 
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as fh:
-                tj = json.load(fh).get(prec)
-            if tj and tj.get("valid"):
-                traffic = tj["bytes_per_cell"] * cells
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(prec, cells)
 
     if rank == 0:
         line = {
