@@ -166,11 +166,16 @@ int lbmhd_bytes_per_cell(int precision);
 /* Number of step-kernel launches issued by this handle since creation. */
 int64_t lbmhd_launch_count(const lbmhd_t* h);
 
-/* Launch shape of the step kernel: vec nodes per thread along x (1, 2 or
- * 4, dividing nx) and block threads per block (multiple of 32, <= 256).
- * The default is the widest vector that divides nx (2 at most for FP64)
- * and 256 threads.  Results do not depend on the shape.  EINVAL if the
- * shape is not available. */
+/* Launch shape of the step kernel.  vec >= 1 selects the register kernel:
+ * vec nodes per thread along x (1, 2 or 4, dividing nx) and block threads
+ * per block (multiple of 32, <= 256).  vec = 0 selects the TMA-staged
+ * kernel (FP32, FP32_DEV, FP16_DEV): persistent CTAs of `block` threads
+ * stream row tiles of `block` nodes (128, 256 or 512, dividing nx) through
+ * a shared-memory ring filled by bulk asynchronous copies.  Default: the
+ * register kernel with 4 nodes per thread in 64-thread blocks (FP32 and
+ * FP16 storage) or 2 nodes in 128-thread blocks (FP64), falling back to
+ * narrower vectors when nx is not a multiple.  Results do not depend on
+ * the shape (bit for bit).  EINVAL if the shape is not available. */
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
 

@@ -146,7 +146,7 @@ __global__ void finite_kernel(const typename Fmt<P>::S* __restrict__ st, int* fl
          c += (long long)gridDim.x * blockDim.x) {
         const double a = dev_of<P>(st[c], 0, inv_scale);
         const double b = dev_of<P>(st[9 * ps + c], 9, inv_scale);
-        if (!isfinite(a) || !isfinite(b)) atomicExch(flag, 1);
+        if (!isfinite(a) || !isfinite(b)) atomicOr(flag, 1);
     }
 }
 

@@ -64,6 +64,23 @@ template <> struct Fmt<P_FP16_DEV> {
     }
 };
 
+// Reciprocal and square root in the arithmetic type.  FP64 keeps the
+// IEEE-rounded operations (the parity mode); FP32 uses the single-
+// instruction hardware approximations (relative error ~1e-7, far below
+// the FP32/FP16 storage rounding the FP32 modes carry anyway).
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Collision parameters in the arithmetic type.
 template <class R>
 struct Coll {
@@ -98,7 +115,7 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c)
     const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
     const R rho = R(1) + drho;
-    const R irho = R(1) / rho;
+    const R irho = rcp(rho);
     const R ux = jx * irho, uy = jy * irho;
     const R bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
     const R by = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
@@ -123,14 +140,14 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c)
     const R E = ux * by - uy * bx;
     R tau_e = c.tn, tau_m = c.te;
     if (c.les) {
-        const R Q = sqrt(n4 * n4 + R(4) * (n3 * n3));
-        tau_e = R(0.5) * (c.tn + sqrt(c.tn2 + c.k18 * Q * irho));
+        const R Q = sqrt_(n4 * n4 + R(4) * (n3 * n3));
+        tau_e = R(0.5) * (c.tn + sqrt_(c.tn2 + c.k18 * Q * irho));
         const R Ny1 = g[3] - g[7];
         const R Nx2 = g[4] - g[8];
         const R J = fabs(Ny1 - Nx2 - R(2) * E);
-        tau_m = R(0.5) * (c.te + sqrt(c.te2 + c.k36 * J));
+        tau_m = R(0.5) * (c.te + sqrt_(c.te2 + c.k36 * J));
     }
-    const R snu = R(1) / tau_e;
+    const R snu = rcp(tau_e);
     const R s7 = c.s7 > R(0) ? c.s7 : snu;
     const R s8 = c.s8 > R(0) ? c.s8 : snu;
 
@@ -152,7 +169,7 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c)
     d[7] -= (a3 - a5) - (a6 - q78);
     d[8] -= (a5 - a3) - (a6 - q78);
 
-    const R sm = R(1) / tau_m;
+    const R sm = rcp(tau_m);
     const R third = R(1) / R(3), sixth = R(1) / R(6);
     const R e3 = R(3) * E;
     const R geq[10] = {third * bx,        third * by,          // k = 0

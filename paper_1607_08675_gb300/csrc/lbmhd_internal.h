@@ -7,7 +7,7 @@
 
 #include <string>
 
-#include "../../include/lbmhd.h"
+#include "lbmhd.h"
 
 namespace lbmhd {
 
@@ -38,6 +38,12 @@ cudaError_t launch_step(int prec, int vec, int block, int max_blocks, const void
                         const Geom& g, const HostColl& c, cudaStream_t st);
 bool step_variant_ok(int prec, int vec, int nx);
 
+// TMA-staged step (lbmhd_step_tma.cu): W threads = nodes per row tile,
+// persistent grid of `grid` CTAs; a timed-out wait sets bit 2 of *status.
+bool tma_variant_ok(int prec, int W, int nx);
+cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
+                            const HostColl& c, int* status, cudaStream_t st);
+
 // Equilibrium initialisation from five FP64 device fields.
 cudaError_t launch_init(int prec, const double* rho, const double* ux, const double* uy,
                         const double* bx, const double* by, void* state, const Geom& g,
@@ -51,8 +57,8 @@ cudaError_t launch_get_state(int prec, const void* state, double* out, const Geo
                              const HostColl& c, cudaStream_t st);
 cudaError_t launch_set_state(int prec, const double* in, void* state, const Geom& g,
                              const HostColl& c, cudaStream_t st);
-// Sets *flag to 1 if the density or the magnetic rest population is not
-// finite anywhere.
+// Sets bit 1 of *flag if the density or the magnetic rest population is
+// not finite anywhere.
 cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Geom& g,
                                 const HostColl& c, cudaStream_t st);
 
@@ -82,7 +88,9 @@ struct lbmhd_t {
     double* d_partials;
     double* d_diag;
     int* d_flag;
-    int vec, block;
+    int vec, block;   // register kernel: nodes per thread, threads per block
+    int tma_w;        // > 0: TMA-staged kernel with this tile width
+    int sm_count;
     cudaGraphExec_t graph;
     int graph_steps;
 };

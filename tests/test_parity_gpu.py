@@ -96,20 +96,31 @@ def test_fp64_ragged_and_degenerate_shapes(L, orc, shape):
     assert np.max(np.abs(st - ref)) < 1e-14
 
 
+SHAPES = ((1, 256), (2, 128), (4, 64), (4, 256), (1, 32), (2, 96), (0, 128), (0, 256), (0, 512))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev"])
-def test_launch_shapes_give_identical_results(L, prec):
-    """The result does not depend on vector width or block size (each node
-    is computed by the same arithmetic wherever it sits in a warp)."""
-    fields = inputs.orszag_tang(128, 40, seed=1)
-    base = None
-    for launch in ((1, 256), (2, 128), (4, 64), (4, 256), (1, 32), (2, 96)):
-        if prec == "fp64" and launch[0] == 4:
+@pytest.mark.parametrize("shape", [(512, 40), (256, 3), (128, 1), (1024, 2)])
+def test_launch_shapes_give_identical_results(L, prec, shape):
+    """The result does not depend on the kernel or its launch shape: the
+    register kernel at every vector width and block size and the TMA-staged
+    kernel at every tile width (including one tile per row, where both
+    periodic granules wrap, and one-row lattices) give the same bits."""
+    nx, ny = shape
+    fields = inputs.orszag_tang(nx, ny, seed=1)
+    base, n = None, 0
+    for launch in SHAPES:
+        if prec == "fp64" and launch[0] in (0, 4):
+            continue
+        if launch[0] == 0 and nx % launch[1]:
             continue
         _, st, _ = run_gpu(L, fields, 70, precision=prec, launch=launch, **PRESETS["les"])
+        n += 1
         if base is None:
             base = st
         else:
             assert np.array_equal(st, base), launch
+    assert n >= 4
 
 
 def test_graph_replay_equals_single_launches(L):
