@@ -210,6 +210,75 @@ int lbmhd_diagnostics_noalloc(const void* state, int precision, int nx, int ny,
 /* Free everything the handle owns.  NULL is accepted. */
 void lbmhd_destroy(lbmhd_t* h);
 
+/* ---- ensembles: many independent lattices advanced together ------------
+ * A batch holds nruns periodic lattices of their own sizes, each with its
+ * own tau_nu, tau_eta and C_S (every other parameter from `common`), and
+ * advances all of them by the same step of Sec. 1.2 / Sec. 3 in one
+ * persistent kernel: co-resident CTAs sweep the work units of every run,
+ * meet at a grid barrier, and continue with the next step
+ * (steps_per_launch steps per launch); long runs replay a captured CUDA
+ * graph of such launches.  Each run evolves bit-identically to an lbmhd_t
+ * with the same parameters.  The grid-barrier wait is bounded (about one
+ * second); on expiry the step reports LBMHD_ETIMEOUT at the next
+ * synchronising call and every run must be re-initialised. */
+typedef struct lbmhd_batch_t lbmhd_batch_t;
+
+/* Arrays of nruns entries (caller-owned, not retained).  Every run is
+ * validated as lbmhd_create validates one lattice; the ensemble may hold
+ * at most 2^31 nodes.  Allocates both population buffers. */
+int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* tau_nu,
+                       const double* tau_eta, const double* C_S, const lbmhd_params* common,
+                       lbmhd_batch_t** out);
+
+/* Equilibrium initialisation of run `run` from five host fields (as
+ * lbmhd_init).  Every run must be initialised before lbmhd_batch_step. */
+int lbmhd_batch_init(lbmhd_batch_t* b, int run, const double* rho, const double* ux,
+                     const double* uy, const double* bx, const double* by);
+
+/* Advance every run by n steps (asynchronous on the batch's stream). */
+int lbmhd_batch_step(lbmhd_batch_t* b, int n);
+
+/* Host moments / FP64 populations of one run (layouts as lbmhd_moments and
+ * lbmhd_get_state); synchronise. */
+int lbmhd_batch_moments(lbmhd_batch_t* b, int run, double* rho, double* ux, double* uy,
+                        double* bx, double* by);
+int lbmhd_batch_get_state(lbmhd_batch_t* b, int run, double* state);
+
+/* Wait for the batch's stream; reports ETIMEOUT / ENONFINITE. */
+int lbmhd_batch_sync(lbmhd_batch_t* b);
+
+/* Work shape: vec nodes per thread (1, 2, 4; must divide every run's nx),
+ * block threads per work unit (multiple of 32, <= 256), steps per
+ * persistent launch (1..4096).  Results do not depend on the shape. */
+int lbmhd_batch_set_launch(lbmhd_batch_t* b, int vec, int block, int steps_per_launch);
+int lbmhd_batch_get_launch(const lbmhd_batch_t* b, int* vec, int* block, int* steps_per_launch);
+
+/* Autotuner: times every available (vec, block, steps_per_launch) for
+ * trial_steps steps on a rest state and keeps the fastest.  Results are
+ * cached in the JSON file cache_path (key: GPU name, precision, the
+ * multiset of lattice shapes); a cached key is applied without timing.
+ * cache_path may be NULL (no cache).  Must run before any
+ * lbmhd_batch_init (ESTATE otherwise); best_mlups (may be NULL) receives
+ * the winner's throughput. */
+int lbmhd_batch_autotune(lbmhd_batch_t* b, const char* cache_path, int trial_steps,
+                         double* best_mlups);
+
+/* Counters (host, no synchronisation): steps since the last init, and
+ * persistent-kernel launches since creation. */
+int64_t lbmhd_batch_step_count(const lbmhd_batch_t* b);
+int64_t lbmhd_batch_launch_count(const lbmhd_batch_t* b);
+
+/* Fault injection for tests of failure detection.  With
+ * LBMHD_DEBUG_DROP_BARRIER_ARRIVAL one CTA leaves the persistent kernel
+ * before its first grid barrier, so the others' bounded waits expire and
+ * the next synchronising call returns LBMHD_ETIMEOUT (the GPU context stays
+ * usable).  0 clears it. */
+#define LBMHD_DEBUG_DROP_BARRIER_ARRIVAL 1
+int lbmhd_batch_debug(lbmhd_batch_t* b, int flags);
+
+/* Free everything the batch owns.  NULL is accepted. */
+void lbmhd_batch_destroy(lbmhd_batch_t* b);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* lbmhd_last_error(void);
 

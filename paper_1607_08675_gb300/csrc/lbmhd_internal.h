@@ -69,6 +69,10 @@ cudaError_t launch_diag(int prec, const void* state, double* partials, double* o
 
 void set_error(const std::string& msg);
 
+// Parameter validation shared by lbmhd_create and lbmhd_batch_create
+// (status code; message through set_error).
+int validate_params(int nx, int ny, const lbmhd_params* p);
+
 }  // namespace lbmhd
 
 struct lbmhd_t {

@@ -60,7 +60,9 @@ int cuda_fail(lbmhd_t* h, cudaError_t e, const char* where) {
 
 bool is_finite(double v) { return std::isfinite(v); }
 
-int validate(int nx, int ny, const lbmhd_params* p) {
+}  // namespace
+
+int lbmhd::validate_params(int nx, int ny, const lbmhd_params* p) {
     if (!p) return fail(LBMHD_EINVAL, "params is NULL");
     if (p->abi_version != LBMHD_ABI_VERSION)
         return fail(LBMHD_EVERSION, "params.abi_version does not match LBMHD_ABI_VERSION");
@@ -87,6 +89,8 @@ int validate(int nx, int ny, const lbmhd_params* p) {
     if (!(xi > 0.0)) return fail(LBMHD_EINVAL, "s7, s8 give a non-positive bulk viscosity");
     return LBMHD_OK;
 }
+
+namespace {
 
 HostColl make_coll(const lbmhd_params* p) {
     HostColl c;
@@ -172,7 +176,7 @@ int lbmhd_bytes_per_cell(int precision) { return (int)(2 * kNumPlanes * storage_
 
 int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     if (!out) return fail(LBMHD_EINVAL, "out is NULL");
-    int rc = validate(nx, ny, p);
+    int rc = validate_params(nx, ny, p);
     if (rc) return rc;
     lbmhd_t* h = new (std::nothrow) lbmhd_t();
     if (!h) return fail(LBMHD_ENOMEM, "host allocation failed");

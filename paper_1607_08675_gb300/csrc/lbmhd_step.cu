@@ -1,40 +1,14 @@
 // lbmhd_step.cu -- the fused pull-stream + collide kernel of one LB-MHD
-// time step (Sec. 1.2 streaming, Sec. 3 MRT / SRT collisions).
-//
-// Layout: 19 SoA planes per buffer, x fastest.  A warp covers 32*V
-// consecutive nodes of one row; each thread loads V nodes of every plane
-// with one aligned vector load.  The pull of an x-shifted plane needs the
-// element just left (c_x = +1) or right (c_x = -1) of the thread's
-// segment: it comes from the neighbouring lane by a warp shuffle, and only
-// a lane at a warp edge or at the periodic wrap loads it from memory.  All
-// HBM traffic is therefore the 19 coalesced plane reads and 19 plane
-// writes per node; the collision runs in registers.
-#include "lbmhd_device.cuh"
+// time step over a single lattice (Sec. 1.2 streaming, Sec. 3 MRT / SRT
+// collisions).  The per-thread work is step_body (lbmhd_step_body.cuh): a
+// warp covers 32*V consecutive nodes of one row, loads each of the 19
+// planes once with aligned vector loads, takes the x-halo from the
+// neighbouring lane by a shuffle and collides in registers.  All HBM
+// traffic is the 19 plane reads and 19 plane writes per node.
 #include "lbmhd_internal.h"
+#include "lbmhd_step_body.cuh"
 
 namespace lbmhd {
-
-template <class S, int V>
-struct alignas(sizeof(S) * V) Pack {
-    S v[V];
-};
-
-template <class S>
-__device__ __forceinline__ S shfl_up1(S v) {
-    return __shfl_up_sync(0xffffffffu, v, 1);
-}
-template <>
-__device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
-    return (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)v, 1);
-}
-template <class S>
-__device__ __forceinline__ S shfl_down1(S v) {
-    return __shfl_down_sync(0xffffffffu, v, 1);
-}
-template <>
-__device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
-    return (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)v, 1);
-}
 
 template <int P, int V>
 __global__ void __launch_bounds__(256) step_kernel(const typename Fmt<P>::S* __restrict__ src,
@@ -43,89 +17,14 @@ __global__ void __launch_bounds__(256) step_kernel(const typename Fmt<P>::S* __r
                                                    unsigned total_pad,
                                                    Coll<typename Fmt<P>::R> c, float scale,
                                                    float inv_scale) {
-    using S = typename Fmt<P>::S;
-    using R = typename Fmt<P>::R;
-    const int lane = threadIdx.x & 31;
-    const unsigned nxv = (unsigned)(nx / V);
     const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride) {
-        const bool live = t < total;
-        const unsigned tc = live ? t : total - 1;
-        const int y = (int)(tc / nxv);
-        const int x0 = (int)(tc - (unsigned)y * nxv) * V;
-        const int ym = y == 0 ? ny - 1 : y - 1;
-        const int yp = y == ny - 1 ? 0 : y + 1;
-        const bool has_left = lane > 0 && x0 > 0;
-        const bool has_right = lane < 31 && x0 + V < nx;
-        const int xl = x0 == 0 ? nx - 1 : x0 - 1;
-        const int xr = x0 + V == nx ? 0 : x0 + V;
-
-        S raw[kPlanes][V];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) {
-            const int cx = plane_cx(p), cy = plane_cy(p);
-            const int row = cy == 0 ? y : (cy > 0 ? ym : yp);
-            const S* base = src + p * ps + (long long)row * nx;
-            const Pack<S, V> pk = *reinterpret_cast<const Pack<S, V>*>(base + x0);
-            if (cx == 0) {
-#pragma unroll
-                for (int k = 0; k < V; ++k) raw[p][k] = pk.v[k];
-            } else if (cx > 0) {
-                S prev = shfl_up1(pk.v[V - 1]);
-                if (!has_left) prev = base[xl];
-                raw[p][0] = prev;
-#pragma unroll
-                for (int k = 1; k < V; ++k) raw[p][k] = pk.v[k - 1];
-            } else {
-                S next = shfl_down1(pk.v[0]);
-                if (!has_right) next = base[xr];
-#pragma unroll
-                for (int k = 0; k < V - 1; ++k) raw[p][k] = pk.v[k + 1];
-                raw[p][V - 1] = next;
-            }
-        }
-
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            R d[9], g[10];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i] = Fmt<P>::dec(raw[i][k], i, inv_scale);
-#pragma unroll
-            for (int q = 0; q < 10; ++q) g[q] = Fmt<P>::dec(raw[9 + q][k], 9 + q, inv_scale);
-            collide<R>(d, g, c);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) raw[i][k] = Fmt<P>::enc(d[i], i, scale);
-#pragma unroll
-            for (int q = 0; q < 10; ++q) raw[9 + q][k] = Fmt<P>::enc(g[q], 9 + q, scale);
-        }
-
-        if (live) {
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p) {
-                Pack<S, V> o;
-#pragma unroll
-                for (int k = 0; k < V; ++k) o.v[k] = raw[p][k];
-                *reinterpret_cast<Pack<S, V>*>(dst + p * ps + (long long)y * nx + x0) = o;
-            }
-        }
-    }
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride)
+        step_body<P, V>(src, dst, nx, ny, ps, t, total, c, scale, inv_scale);
 }
 
 template <class R>
 static Coll<R> to_coll(const HostColl& h) {
-    Coll<R> c;
-    c.tn = (R)h.tn;
-    c.te = (R)h.te;
-    c.tn2 = (R)(h.tn * h.tn);
-    c.te2 = (R)(h.te * h.te);
-    c.k18 = (R)h.k18;
-    c.k36 = (R)h.k36;
-    c.s5 = (R)h.s5;
-    c.s6 = (R)h.s6;
-    c.s7 = (R)h.s7;
-    c.s8 = (R)h.s8;
-    c.les = h.les;
-    return c;
+    return make_coll_t<R>(h.tn, h.te, h.k18, h.k36, h.s5, h.s6, h.s7, h.s8, h.les);
 }
 
 template <int P, int V>

@@ -1,0 +1,134 @@
+// lbmhd_step_body.cuh -- the per-thread work of one fused stream-collide
+// step over V consecutive nodes of a row, shared by the single-lattice
+// kernel (lbmhd_step.cu) and the batched ensemble kernel (lbmhd_batch.cu)
+// so that both compute bit-identical results.
+//
+// Layout: 19 SoA planes, x fastest.  Thread t of a lattice covers nodes
+// (y, x0 .. x0 + V - 1) with y = t / (nx / V), x0 = (t mod (nx / V)) V; the
+// 32 lanes of a warp hold consecutive t.  Each plane is read with one
+// aligned vector load; an x-shifted plane gets its missing edge element
+// from the neighbouring lane by a warp shuffle, and only a lane at a warp
+// edge or at the periodic wrap loads it from memory.  The collision runs in
+// registers.
+#pragma once
+
+#include "lbmhd_device.cuh"
+
+namespace lbmhd {
+
+template <class S, int V>
+struct alignas(sizeof(S) * V) Pack {
+    S v[V];
+};
+
+template <class S>
+__device__ __forceinline__ S shfl_up1(S v) {
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <>
+__device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
+    return (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)v, 1);
+}
+template <class S>
+__device__ __forceinline__ S shfl_down1(S v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+template <>
+__device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
+    return (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)v, 1);
+}
+
+// One thread's step.  All 32 lanes of the warp must call it together
+// (shuffles); t >= total marks a padding thread, which loads valid
+// addresses (those of thread total - 1) and stores nothing.
+template <int P, int V>
+__device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__ src,
+                                          typename Fmt<P>::S* __restrict__ dst, int nx, int ny,
+                                          long long ps, unsigned t, unsigned total,
+                                          const Coll<typename Fmt<P>::R>& c, float scale,
+                                          float inv_scale) {
+    using S = typename Fmt<P>::S;
+    using R = typename Fmt<P>::R;
+    const int lane = threadIdx.x & 31;
+    const unsigned nxv = (unsigned)(nx / V);
+    const bool live = t < total;
+    const unsigned tc = live ? t : total - 1;
+    const int y = (int)(tc / nxv);
+    const int x0 = (int)(tc - (unsigned)y * nxv) * V;
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const bool has_left = lane > 0 && x0 > 0;
+    const bool has_right = lane < 31 && x0 + V < nx;
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xr = x0 + V == nx ? 0 : x0 + V;
+
+    S raw[kPlanes][V];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = plane_cx(p), cy = plane_cy(p);
+        const int row = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const S* base = src + p * ps + (long long)row * nx;
+        const Pack<S, V> pk = *reinterpret_cast<const Pack<S, V>*>(base + x0);
+        if (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) raw[p][k] = pk.v[k];
+        } else if (cx > 0) {
+            S prev = shfl_up1(pk.v[V - 1]);
+            if (!has_left) prev = base[xl];
+            raw[p][0] = prev;
+#pragma unroll
+            for (int k = 1; k < V; ++k) raw[p][k] = pk.v[k - 1];
+        } else {
+            S next = shfl_down1(pk.v[0]);
+            if (!has_right) next = base[xr];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) raw[p][k] = pk.v[k + 1];
+            raw[p][V - 1] = next;
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        R d[9], g[10];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = Fmt<P>::dec(raw[i][k], i, inv_scale);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = Fmt<P>::dec(raw[9 + q][k], 9 + q, inv_scale);
+        collide<R>(d, g, c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) raw[i][k] = Fmt<P>::enc(d[i], i, scale);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) raw[9 + q][k] = Fmt<P>::enc(g[q], 9 + q, scale);
+    }
+
+    if (live) {
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            Pack<S, V> o;
+#pragma unroll
+            for (int k = 0; k < V; ++k) o.v[k] = raw[p][k];
+            *reinterpret_cast<Pack<S, V>*>(dst + p * ps + (long long)y * nx + x0) = o;
+        }
+    }
+}
+
+template <class R>
+__host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18, double k36,
+                                               double s5, double s6, double s7, double s8,
+                                               int les) {
+    Coll<R> c;
+    c.tn = (R)tn;
+    c.te = (R)te;
+    c.tn2 = (R)(tn * tn);
+    c.te2 = (R)(te * te);
+    c.k18 = (R)k18;
+    c.k36 = (R)k36;
+    c.s5 = (R)s5;
+    c.s6 = (R)s6;
+    c.s7 = (R)s7;
+    c.s8 = (R)s8;
+    c.les = les;
+    return c;
+}
+
+}  // namespace lbmhd

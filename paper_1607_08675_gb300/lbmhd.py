@@ -84,6 +84,21 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_diagnostics_noalloc": (i, [vp, i, i, i, ctypes.c_longlong, d, vp, vp]),
                 "lbmhd_destroy": (None, [h]),
                 "lbmhd_last_error": (ctypes.c_char_p, []),
+                "lbmhd_batch_create": (i, [i, vp, vp, vp, vp, vp, ctypes.POINTER(Params), pp]),
+                "lbmhd_batch_init": (i, [h, i, vp, vp, vp, vp, vp]),
+                "lbmhd_batch_step": (i, [h, i]),
+                "lbmhd_batch_moments": (i, [h, i, vp, vp, vp, vp, vp]),
+                "lbmhd_batch_get_state": (i, [h, i, vp]),
+                "lbmhd_batch_sync": (i, [h]),
+                "lbmhd_batch_set_launch": (i, [h, i, i, i]),
+                "lbmhd_batch_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i),
+                                                ctypes.POINTER(i)]),
+                "lbmhd_batch_autotune": (i, [h, ctypes.c_char_p, i,
+                                              ctypes.POINTER(ctypes.c_double)]),
+                "lbmhd_batch_step_count": (ctypes.c_int64, [h]),
+                "lbmhd_batch_launch_count": (ctypes.c_int64, [h]),
+                "lbmhd_batch_debug": (i, [h, i]),
+                "lbmhd_batch_destroy": (None, [h]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -277,3 +292,105 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---- ensembles -------------------------------------------------------------
+
+DEBUG_DROP_BARRIER_ARRIVAL = 1
+
+
+class BatchHandle:
+    """An lbmhd_batch_t* with its runs' shapes."""
+
+    def __init__(self, ptr: int, shapes, params: Params):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.shapes = [tuple(s) for s in shapes]  # (ny, nx) per run
+        self.params = params
+
+    @property
+    def nruns(self):
+        return len(self.shapes)
+
+
+def lbmhd_batch_create(nx, ny, tau_nu, tau_eta, C_S, params: Params | None = None) -> BatchHandle:
+    """nx, ny, tau_nu, tau_eta, C_S: sequences with one entry per run."""
+    params = params if params is not None else lbmhd_params_default()
+    n = len(nx)
+    ai = lambda v: np.ascontiguousarray(v, dtype=np.int32)
+    ad = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    arrs = [ai(nx), ai(ny), ad(tau_nu), ad(tau_eta), ad(C_S)]
+    if any(len(a) != n for a in arrs):
+        raise ValueError("per-run sequences must have equal length")
+    out = ctypes.c_void_p()
+    _check(lib().lbmhd_batch_create(n, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                    ctypes.byref(params), ctypes.byref(out)))
+    return BatchHandle(out.value, list(zip(arrs[1].tolist(), arrs[0].tolist())), params)
+
+
+def _run_shape(b: BatchHandle, run: int):
+    if not 0 <= run < b.nruns:
+        raise LBMHDError(-1, f"run index {run} out of range [0, {b.nruns})")
+    return b.shapes[run]
+
+
+def lbmhd_batch_init(b: BatchHandle, run: int, rho, ux, uy, bx, by):
+    arrs = [_host(a, _run_shape(b, run)) for a in (rho, ux, uy, bx, by)]
+    _check(lib().lbmhd_batch_init(b.ptr, int(run),
+                                  *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs]))
+
+
+def lbmhd_batch_step(b: BatchHandle, n: int = 1):
+    _check(lib().lbmhd_batch_step(b.ptr, int(n)))
+
+
+def lbmhd_batch_moments(b: BatchHandle, run: int):
+    out = [np.empty(_run_shape(b, run)) for _ in range(5)]
+    _check(lib().lbmhd_batch_moments(b.ptr, int(run),
+                                     *[a.ctypes.data_as(ctypes.c_void_p) for a in out]))
+    return tuple(out)
+
+
+def lbmhd_batch_get_state(b: BatchHandle, run: int) -> np.ndarray:
+    st = np.empty((19,) + _run_shape(b, run))
+    _check(lib().lbmhd_batch_get_state(b.ptr, int(run), st.ctypes.data_as(ctypes.c_void_p)))
+    return st
+
+
+def lbmhd_batch_sync(b: BatchHandle):
+    _check(lib().lbmhd_batch_sync(b.ptr))
+
+
+def lbmhd_batch_set_launch(b: BatchHandle, vec: int, block: int, steps_per_launch: int):
+    _check(lib().lbmhd_batch_set_launch(b.ptr, int(vec), int(block), int(steps_per_launch)))
+
+
+def lbmhd_batch_get_launch(b: BatchHandle):
+    v, bl, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbmhd_batch_get_launch(b.ptr, ctypes.byref(v), ctypes.byref(bl), ctypes.byref(s)))
+    return v.value, bl.value, s.value
+
+
+def lbmhd_batch_autotune(b: BatchHandle, cache_path: str | None = None,
+                         trial_steps: int = 16) -> float:
+    best = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().lbmhd_batch_autotune(b.ptr, path, int(trial_steps), ctypes.byref(best)))
+    return best.value
+
+
+def lbmhd_batch_step_count(b: BatchHandle) -> int:
+    return int(lib().lbmhd_batch_step_count(b.ptr))
+
+
+def lbmhd_batch_launch_count(b: BatchHandle) -> int:
+    return int(lib().lbmhd_batch_launch_count(b.ptr))
+
+
+def lbmhd_batch_debug(b: BatchHandle, flags: int):
+    _check(lib().lbmhd_batch_debug(b.ptr, int(flags)))
+
+
+def lbmhd_batch_destroy(b: BatchHandle):
+    if b is not None and b.ptr:
+        lib().lbmhd_batch_destroy(b.ptr)
+        b.ptr = ctypes.c_void_p()

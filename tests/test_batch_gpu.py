@@ -1,0 +1,171 @@
+"""The batched ensemble (lbmhd_batch_*): one persistent kernel advancing
+runs of uneven sizes, each with its own C_S and relaxation times.
+
+Every run must evolve bit for bit like its own single lattice (the same
+per-thread step code runs in both kernels), and in FP64 match the oracle to
+the 1e-12 bar.  The grid barrier's bounded wait is exercised by dropping
+one CTA's arrival (host-requested fault injection): the step must report
+ETIMEOUT without hanging, and the batch must work again after re-init.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1607_08675_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RUNS = [  # (nx, ny, tau_nu, tau_eta, C_S)
+    (128, 64, 0.6, 0.65, 0.10),
+    (256, 128, 0.52, 0.55, 0.20),
+    (64, 64, 0.7, 0.6, 0.05),
+    (192, 40, 0.55, 0.58, 0.15),
+    (128, 1, 0.6, 0.6, 0.10),
+]
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_08675_gb300 import build, lbmhd
+
+    build.build()
+    return lbmhd
+
+
+def make_batch(L, runs, prec="fp32", launch=None):
+    nx, ny, tn, te, cs = zip(*runs)
+    b = L.lbmhd_batch_create(nx, ny, tn, te, cs, L.lbmhd_params_default(precision=prec))
+    if launch:
+        L.lbmhd_batch_set_launch(b, *launch)
+    fields = [inputs.orszag_tang(r[0], r[1], seed=10 + i) for i, r in enumerate(runs)]
+    for i, f in enumerate(fields):
+        L.lbmhd_batch_init(b, i, *f)
+    return b, fields
+
+
+def single(L, run, fields, steps, prec):
+    nx, ny, tn, te, cs = run
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision=prec, tau_nu=tn, tau_eta=te,
+                                                      C_S=cs))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, steps)
+    st = L.lbmhd_get_state(h)
+    L.lbmhd_destroy(h)
+    return st
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16_dev", "fp64"])
+def test_batch_runs_equal_single_lattices_bitwise(L, prec):
+    steps = 150  # exercises graph replays and a direct tail
+    b, fields = make_batch(L, RUNS, prec)
+    L.lbmhd_batch_step(b, steps)
+    assert L.lbmhd_batch_step_count(b) == steps
+    for i, run in enumerate(RUNS):
+        got = L.lbmhd_batch_get_state(b, i)
+        ref = single(L, run, fields[i], steps, prec)
+        assert np.array_equal(got, ref), (prec, run)
+    L.lbmhd_batch_destroy(b)
+
+
+def test_batch_fp64_matches_oracle(L, orc):
+    runs = RUNS[:3]
+    b, fields = make_batch(L, runs, "fp64")
+    L.lbmhd_batch_step(b, 200)
+    for i, (nx, ny, tn, te, cs) in enumerate(runs):
+        ref = orc.step(orc.init(*fields[i]), orc.params(tau_nu=tn, tau_eta=te, C_S=cs), 200)
+        m = L.lbmhd_batch_moments(b, i)
+        for k, (a, r) in enumerate(zip(m, orc.moments(ref))):
+            if k == 0:
+                a, r = a - 1, r - 1
+            assert np.max(np.abs(a - r)) < 1e-12 * np.max(np.abs(r)), (i, k)
+    L.lbmhd_batch_destroy(b)
+
+
+def test_batch_launch_shapes_identical(L):
+    runs = [(128, 48, 0.6, 0.62, 0.1), (64, 32, 0.55, 0.6, 0.2)]
+    base = None
+    for launch in ((4, 64, 8), (2, 128, 1), (1, 256, 64), (4, 32, 3), (2, 96, 5)):
+        b, _ = make_batch(L, runs, "fp32", launch)
+        L.lbmhd_batch_step(b, 77)
+        st = [L.lbmhd_batch_get_state(b, i) for i in range(len(runs))]
+        assert L.lbmhd_batch_get_launch(b) == launch
+        L.lbmhd_batch_destroy(b)
+        if base is None:
+            base = st
+        else:
+            for a, c in zip(st, base):
+                assert np.array_equal(a, c), launch
+
+
+def test_batch_autotune_and_cache(L, tmp_path):
+    runs = [(128, 128, 0.6, 0.6, 0.1)] * 3 + [(256, 256, 0.55, 0.55, 0.15)]
+    nx, ny, tn, te, cs = zip(*runs)
+    cache = str(tmp_path / "tune.json")
+    b = L.lbmhd_batch_create(nx, ny, tn, te, cs, L.lbmhd_params_default(precision="fp32"))
+    best = L.lbmhd_batch_autotune(b, cache, 8)
+    shape = L.lbmhd_batch_get_launch(b)
+    assert best > 0
+    data = json.load(open(cache))
+    assert len(data) == 1
+    entry = list(data.values())[0]
+    assert tuple(entry[:3]) == shape
+    # the tuned batch still runs correctly
+    f = [inputs.orszag_tang(r[0], r[1], seed=i) for i, r in enumerate(runs)]
+    for i in range(len(runs)):
+        L.lbmhd_batch_init(b, i, *f[i])
+    L.lbmhd_batch_step(b, 20)
+    assert np.array_equal(L.lbmhd_batch_get_state(b, 3), single(L, runs[3], f[3], 20, "fp32"))
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd_batch_autotune(b, cache, 8)  # after init
+    assert e.value.code == -7
+    L.lbmhd_batch_destroy(b)
+    # a second batch of the same shapes takes the cached choice
+    b2 = L.lbmhd_batch_create(nx, ny, tn, te, cs, L.lbmhd_params_default(precision="fp32"))
+    assert L.lbmhd_batch_autotune(b2, cache, 8) == pytest.approx(entry[3])
+    assert L.lbmhd_batch_get_launch(b2) == shape
+    L.lbmhd_batch_destroy(b2)
+
+
+def test_batch_barrier_timeout_is_reported_not_hung(L):
+    """Failure detection: a CTA that never arrives at the grid barrier makes
+    the others' bounded waits expire (~1 s); the next synchronising call
+    returns ETIMEOUT and the context stays usable."""
+    import time
+
+    runs = RUNS[:2]
+    b, fields = make_batch(L, runs, "fp32", (4, 64, 4))
+    L.lbmhd_batch_debug(b, L.DEBUG_DROP_BARRIER_ARRIVAL)
+    t0 = time.time()
+    L.lbmhd_batch_step(b, 4)
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd_batch_sync(b)
+    assert e.value.code == -5
+    assert time.time() - t0 < 30
+    # state is undefined now: stepping needs a fresh init
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd_batch_step(b, 1)
+    assert e.value.code == -7
+    L.lbmhd_batch_debug(b, 0)
+    for i, f in enumerate(fields):
+        L.lbmhd_batch_init(b, i, *f)
+    L.lbmhd_batch_step(b, 10)
+    assert np.array_equal(L.lbmhd_batch_get_state(b, 1), single(L, runs[1], fields[1], 10, "fp32"))
+    L.lbmhd_batch_destroy(b)
+
+
+def test_batch_rejects_bad_runs(L):
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_batch_create([64, 64], [64, 64], [0.6, 0.5], [0.6, 0.6], [0.1, 0.1])
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_batch_create([64, 0], [64, 64], [0.6, 0.6], [0.6, 0.6], [0.1, 0.1])
+    b, _ = make_batch(L, RUNS[:2])
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_batch_set_launch(b, 4, 64, 0)
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_batch_init(b, 5, *inputs.orszag_tang(128, 64))
+    L.lbmhd_batch_destroy(b)

@@ -193,7 +193,7 @@ def test_full_size_turbulence_sampled_one_step(L, orc):
     rng = np.random.default_rng(0)
     idx = np.concatenate([rng.integers(0, n * n, 4000),
                           [0, n - 1, n * n - 1, n * (n - 1), n * 512 + 1023, 1023 * n + 511]])
-    kw = dict(tau_nu=0.51, tau_eta=0.51, C_S=0.1)
+    kw = dict(tau_nu=0.51, tau_eta=0.51, C_S=0.1, s5=1.2, s6=1.2, s7=1.3, s8=1.3)
     for prec, tol in (("fp64", 1e-13), ("fp32", 2e-7)):
         h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
         L.lbmhd_init(h, *fields)
