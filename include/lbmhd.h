@@ -210,6 +210,38 @@ int lbmhd_diagnostics_noalloc(const void* state, int precision, int nx, int ny,
 /* Free everything the handle owns.  NULL is accepted. */
 void lbmhd_destroy(lbmhd_t* h);
 
+/* ---- adjoint (discrete, hand-written) ------------------------------------
+ * Gradients of a scalar function of the final moments with respect to
+ * C_S, tau_nu, tau_eta and the initial fields, through the exact transpose
+ * of the discrete step (pull-stream and the collision of Sec. 3 with the
+ * local Smagorinsky rates).  Supported storage: FP64, FP32, FP32_DEV.  The
+ * derivative of |x| and of sqrt at 0 (local |S|, |j| of exactly zero) is
+ * taken as 0. */
+
+/* Initialise from five device fields (as lbmhd_init_device) and advance
+ * nsteps steps, keeping an FP64 checkpoint of the state every `every`
+ * steps in device memory owned by the handle (ceil(nsteps/every) * 19 *
+ * nx*ny doubles, plus a copy of the five fields).  Afterwards the handle
+ * holds the final state.  Replaces any earlier record. */
+int lbmhd_adjoint_record(lbmhd_t* h, const double* rho0, const double* ux0, const double* uy0,
+                         const double* bx0, const double* by0, int nsteps, int every);
+
+/* Back-propagate dL/d(final rho, u_x, u_y, B_x, B_y) (device fields; NULL
+ * means zero) through the recorded run: restore each checkpoint, recompute
+ * the segment with the forward kernel (bit-identical), and apply the
+ * adjoint step backwards.  Writes dtheta[0..2] = dL/dC_S, dL/dtau_nu,
+ * dL/dtau_eta (host, FP64, accumulated in FP64) and, where not NULL, the
+ * device fields dL/d(rho0, ux0, uy0, bx0, by0).  ESTATE without a record or
+ * if the handle stepped since.  Temporary device memory: `every` states in
+ * the storage format and two adjoint states.  Synchronises. */
+int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
+                           const double* g_uy, const double* g_bx, const double* g_by,
+                           double* dtheta, double* d_rho0, double* d_ux0, double* d_uy0,
+                           double* d_bx0, double* d_by0);
+
+/* Free the recorded checkpoints (also done by lbmhd_destroy). */
+int lbmhd_adjoint_release(lbmhd_t* h);
+
 /* ---- ensembles: many independent lattices advanced together ------------
  * A batch holds nruns periodic lattices of their own sizes, each with its
  * own tau_nu, tau_eta and C_S (every other parameter from `common`), and

@@ -181,6 +181,8 @@ HostColl run_coll(const lbmhd_batch_t* b, int r) {
     c.k36 = 36.0 * cd2;
     c.s5 = q.s5 > 0.0 ? q.s5 : 1.0 / q.tau_nu;
     c.s6 = q.s6 > 0.0 ? q.s6 : 1.0 / q.tau_nu;
+    c.tie5 = q.s5 > 0.0 ? 0 : 1;
+    c.tie6 = q.s6 > 0.0 ? 0 : 1;
     c.s7 = q.s7 > 0.0 ? q.s7 : 0.0;
     c.s8 = q.s8 > 0.0 ? q.s8 : 0.0;
     c.les = q.les;

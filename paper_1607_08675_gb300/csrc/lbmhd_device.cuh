@@ -90,6 +90,7 @@ struct Coll {
     R s5, s6;        // resolved energy-flux rates
     R s7, s8;        // fixed rates (used when > 0), else tied to s_nu
     int les;
+    int tie5, tie6;  // s5 (s6) is the tied value 1/tau_nu
 };
 
 // One node: d[9] = streamed f_i - w_i, g[10] = streamed g_k (x, y);

@@ -19,6 +19,7 @@ struct HostColl {
     double tn, te, k18, k36, s5, s6, s7, s8;
     int les;
     float scale, inv_scale;  // FP16_DEV encoding
+    int tie5, tie6;          // s5 / s6 are the tied 1/tau_nu
 };
 
 // Geometry of one lattice in device memory: 19 planes of ps elements each,
@@ -69,6 +70,9 @@ cudaError_t launch_diag(int prec, const void* state, double* partials, double* o
 
 void set_error(const std::string& msg);
 
+// Frees the adjoint tape of a handle (lbmhd_adjoint.cu).
+void free_tape(lbmhd_t* h);
+
 // Parameter validation shared by lbmhd_create and lbmhd_batch_create
 // (status code; message through set_error).
 int validate_params(int nx, int ny, const lbmhd_params* p);
@@ -89,6 +93,7 @@ struct lbmhd_t {
     bool failed;
     int64_t steps;
     int64_t launches;
+    void* tape;  // adjoint checkpoints (lbmhd_adjoint.cu), NULL when none
     double* d_partials;
     double* d_diag;
     int* d_flag;

@@ -101,6 +101,8 @@ HostColl make_coll(const lbmhd_params* p) {
     c.k36 = 36.0 * cd2;
     c.s5 = p->s5 > 0.0 ? p->s5 : 1.0 / p->tau_nu;
     c.s6 = p->s6 > 0.0 ? p->s6 : 1.0 / p->tau_nu;
+    c.tie5 = p->s5 > 0.0 ? 0 : 1;
+    c.tie6 = p->s6 > 0.0 ? 0 : 1;
     c.s7 = p->s7 > 0.0 ? p->s7 : 0.0;
     c.s8 = p->s8 > 0.0 ? p->s8 : 0.0;
     c.les = p->les;
@@ -471,6 +473,7 @@ void lbmhd_destroy(lbmhd_t* h) {
     if (!h) return;
     DeviceGuard dg(h->device);
     if (!h->failed) cudaStreamSynchronize(h->stream);
+    free_tape(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);

@@ -115,7 +115,7 @@ __device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__
 template <class R>
 __host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18, double k36,
                                                double s5, double s6, double s7, double s8,
-                                               int les) {
+                                               int les, int tie5 = 0, int tie6 = 0) {
     Coll<R> c;
     c.tn = (R)tn;
     c.te = (R)te;
@@ -128,6 +128,8 @@ __host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18,
     c.s7 = (R)s7;
     c.s8 = (R)s8;
     c.les = les;
+    c.tie5 = tie5;
+    c.tie6 = tie6;
     return c;
 }
 

@@ -84,6 +84,11 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_diagnostics_noalloc": (i, [vp, i, i, i, ctypes.c_longlong, d, vp, vp]),
                 "lbmhd_destroy": (None, [h]),
                 "lbmhd_last_error": (ctypes.c_char_p, []),
+                "lbmhd_adjoint_record": (i, [h, vp, vp, vp, vp, vp, i, i]),
+                "lbmhd_adjoint_backward": (i, [h, vp, vp, vp, vp, vp,
+                                                ctypes.POINTER(ctypes.c_double),
+                                                vp, vp, vp, vp, vp]),
+                "lbmhd_adjoint_release": (i, [h]),
                 "lbmhd_batch_create": (i, [i, vp, vp, vp, vp, vp, ctypes.POINTER(Params), pp]),
                 "lbmhd_batch_init": (i, [h, i, vp, vp, vp, vp, vp]),
                 "lbmhd_batch_step": (i, [h, i]),
@@ -292,6 +297,40 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---- adjoint -------------------------------------------------------------
+
+
+def _dev_or_null(t, shape):
+    return ctypes.c_void_p(0) if t is None else _dev(t, shape)
+
+
+def lbmhd_adjoint_record(h: Handle, rho0, ux0, uy0, bx0, by0, nsteps: int, every: int):
+    """Initialise from five device fields and run nsteps steps, keeping FP64
+    checkpoints every `every` steps."""
+    _check(lib().lbmhd_adjoint_record(h.ptr, *[_dev(t, h.shape) for t in (rho0, ux0, uy0, bx0, by0)],
+                                      int(nsteps), int(every)))
+
+
+def lbmhd_adjoint_backward(h: Handle, grads, want_fields: bool = True):
+    """grads: dL/d(final rho, ux, uy, bx, by) as CUDA float64 tensors (None =
+    zero).  Returns (dtheta = [dC_S, dtau_nu, dtau_eta], field gradients as a
+    tuple of 5 tensors, or None)."""
+    import torch
+
+    dth = (ctypes.c_double * 3)()
+    outs = None
+    if want_fields:
+        outs = tuple(torch.empty(h.shape, dtype=torch.float64, device="cuda") for _ in range(5))
+    out_ptrs = [ctypes.c_void_p(0)] * 5 if outs is None else [_dev(t, h.shape) for t in outs]
+    _check(lib().lbmhd_adjoint_backward(h.ptr, *[_dev_or_null(g, h.shape) for g in grads], dth,
+                                        *out_ptrs))
+    return [dth[0], dth[1], dth[2]], outs
+
+
+def lbmhd_adjoint_release(h: Handle):
+    _check(lib().lbmhd_adjoint_release(h.ptr))
 
 
 # ---- ensembles -------------------------------------------------------------
