@@ -282,6 +282,61 @@ def run_batched(L, args, stream, rank, hbm, barrier, max_over_ranks):
             "sizes": {str(k): nx.count(k) for k in sorted(set(nx))}}
 
 
+def run_adjoint(args):
+    """The gradient workload: Orszag-Tang 512^2 with the seeded perturbation,
+    tau_nu = tau_eta = 0.6, trial C_S = 0.1; loss = 1/2 sum |u - u_ref|^2 +
+    |B - B_ref|^2 against a run with C_S = 0.12 after 500 steps; FP32
+    forward with FP64 checkpoints every 50 steps, hand-written adjoint
+    backward.  Checked against the FP64 adjoint and a central finite
+    difference of the FP64 forward in C_S."""
+    import torch
+
+    from paper_1607_08675_gb300 import autograd as AG, inputs, lbmhd as L
+
+    n, steps, every = args.adj_n, args.adj_steps, 50
+    f = [torch.tensor(a, dtype=torch.float64, device="cuda")
+         for a in inputs.orszag_tang(n, n, seed=0)]
+    refs = {}
+    with torch.no_grad():
+        for prec in ("fp32", "fp64"):  # the reference run in the trial's precision
+            refs[prec] = AG.rollout(*f, 0.12, 0.6, 0.6, steps, every=every, precision=prec)
+
+    def loss_of(out, prec="fp64"):
+        return 0.5 * sum(((o - r) ** 2).sum() for o, r in zip(out[1:], refs[prec][1:]))
+
+    res = {}
+    for prec in ("fp32", "fp64"):
+        leaves = [t.clone().requires_grad_(True) for t in f]
+        th = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (0.1, 0.6, 0.6)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = AG.rollout(*leaves, *th, steps, every=every, precision=prec)
+        loss = loss_of(out, prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res[prec] = {"loss": loss.item(), "dC_S": th[0].grad.item(),
+                     "dtau_nu": th[1].grad.item(), "dtau_eta": th[2].grad.item(),
+                     "du0_norm": float(torch.linalg.norm(torch.stack([l.grad for l in leaves[1:3]]))),
+                     "dB0_norm": float(torch.linalg.norm(torch.stack([l.grad for l in leaves[3:5]]))),
+                     "forward_s": t1 - t0, "backward_s": t2 - t1}
+    h = 1e-6 * 0.1
+    with torch.no_grad():
+        lp = loss_of(AG.rollout(*f, 0.1 + h, 0.6, 0.6, steps, every=every)).item()
+        lm = loss_of(AG.rollout(*f, 0.1 - h, 0.6, 0.6, steps, every=every)).item()
+    fd = (lp - lm) / (2 * h)
+    r64, r32 = res["fp64"], res["fp32"]
+    return {"workload": f"Orszag-Tang {n}x{n}, {steps} steps, checkpoints every {every}, "
+                        "loss vs C_S = 0.12 run",
+            "fp32": r32, "fp64": r64, "fd_dC_S": fd,
+            "fd_rel_err_fp64": abs(r64["dC_S"] - fd) / abs(fd),
+            "fp32_vs_fp64_rel": {k: abs(r32[k] - r64[k]) / abs(r64[k])
+                                 for k in ("dC_S", "dtau_nu", "dtau_eta", "du0_norm", "dB0_norm")},
+            "node_steps_per_s_fp32": n * n * steps / (r32["forward_s"] + r32["backward_s"])}
+
+
 def shell_spectrum(a, b):
     """Shell-binned spectrum E(k) = 1/2 sum_{k-1/2 <= |k| < k+1/2} |FFT|^2 / N^2 of
     the planar field (a, b)."""
@@ -493,6 +548,11 @@ def run_ours(args):
                "job": f"lbmhd_init (5 host FP64 fields) + lbmhd_step({args.steps}) + "
                       "lbmhd_moments (5 host FP64 fields); bytes amortised per step"}
 
+    # ---- gradients through the hand-written adjoint ------------------------
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = run_adjoint(args)
+
     # ---- batched ensemble vs sequential per-run launches --------------------
     batched = None
     if not args.no_batch:
@@ -524,6 +584,7 @@ def run_ours(args):
                          "bytes_per_cell": bpc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "variants": variants, "batched": batched,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -543,6 +604,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-n", type=int, default=512)
+    ap.add_argument("--adj-steps", type=int, default=500)
     ap.add_argument("--batch-runs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--precision-study", action="store_true",
