@@ -171,11 +171,13 @@ int64_t lbmhd_launch_count(const lbmhd_t* h);
  * per block (multiple of 32, <= 256).  vec = 0 selects the TMA-staged
  * kernel (FP32, FP32_DEV, FP16_DEV): persistent CTAs of `block` threads
  * stream row tiles of `block` nodes (128, 256 or 512, dividing nx) through
- * a shared-memory ring filled by bulk asynchronous copies.  Default: the
- * register kernel with 4 nodes per thread in 64-thread blocks (FP32 and
- * FP16 storage) or 2 nodes in 128-thread blocks (FP64), falling back to
- * narrower vectors when nx is not a multiple.  Results do not depend on
- * the shape (bit for bit).  EINVAL if the shape is not available. */
+ * a shared-memory ring filled by bulk asynchronous copies.  vec = 8 is
+ * available for FP16 storage (16-byte loads).  Default: the register
+ * kernel with 4 nodes per thread in 64-thread blocks (FP32 storage), 8
+ * nodes in 32-thread blocks (FP16 storage) or 2 nodes in 128-thread blocks
+ * (FP64), falling back to narrower vectors when nx is not a multiple.
+ * Results do not depend on the shape (bit for bit).  EINVAL if the shape
+ * is not available. */
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
 

@@ -435,7 +435,7 @@ unsigned adj_grid(long long n) {
 template <class R>
 Coll<R> coll_t(const HostColl& h) {
     return make_coll_t<R>(h.tn, h.te, h.k18, h.k36, h.s5, h.s6, h.s7, h.s8, h.les, h.tie5, h.tie6);
-}
+}  // the adjoint supports unscaled formats only (FP64, FP32, FP32_DEV)
 
 template <int P>
 cudaError_t run_adj_step(const lbmhd_t* h, const void* x, const void* lin, void* lout,

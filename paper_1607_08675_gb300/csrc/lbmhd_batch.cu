@@ -238,7 +238,7 @@ int upload_runs_t(lbmhd_batch_t* b) {
         rd[r].ny = b->ny[r];
         rd[r].total = (unsigned)((long long)b->nx[r] / b->vec * b->ny[r]);
         rd[r].unit0 = unit;
-        rd[r].c = make_coll_t<R>(hc.tn, hc.te, hc.k18, hc.k36, hc.s5, hc.s6, hc.s7, hc.s8, hc.les);
+        rd[r].c = coll_for_prec<R>(hc, b->p.precision);
         const unsigned units = (rd[r].total + b->block - 1) / b->block;
         for (unsigned u = 0; u < units; ++u) map.push_back(r);
         unit += units;

@@ -37,30 +37,35 @@ template <int P> struct Fmt;
 template <> struct Fmt<P_FP64> {
     using S = double;
     using R = double;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest<R>(p); }
     static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest<R>(p); }
 };
 template <> struct Fmt<P_FP32> {
     using S = float;
     using R = float;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest<R>(p); }
     static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest<R>(p); }
 };
 template <> struct Fmt<P_FP32_DEV> {
     using S = float;
     using R = float;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R dec(S v, int, float) { return v; }
     static __device__ __forceinline__ S enc(R d, int, float) { return d; }
 };
+// FP16: stored = d * scale.  The step kernels keep the scaled value through
+// the collision (see collide<R, true>), so dec/enc here convert only.
 template <> struct Fmt<P_FP16_DEV> {
     using S = unsigned short;  // raw binary16 bits
     using R = float;
-    // stored = d * scale; decoded with the exact reciprocal (power of two)
-    static __device__ __forceinline__ R dec(S v, int, float inv_scale) {
-        return __half2float(__ushort_as_half(v)) * inv_scale;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ R dec(S v, int, float) {
+        return __half2float(__ushort_as_half(v));
     }
-    static __device__ __forceinline__ S enc(R d, int, float scale) {
-        return __half_as_ushort(__float2half_rn(d * scale));
+    static __device__ __forceinline__ S enc(R d, int, float) {
+        return __half_as_ushort(__float2half_rn(d));
     }
 };
 
@@ -91,6 +96,7 @@ struct Coll {
     R s7, s8;        // fixed rates (used when > 0), else tied to s_nu
     int les;
     int tie5, tie6;  // s5 (s6) is the tied value 1/tau_nu
+    R inv_s;         // scaled storage: 1 / scale (k18, k36 already divided by scale)
 };
 
 // One node: d[9] = streamed f_i - w_i, g[10] = streamed g_k (x, y);
@@ -110,12 +116,17 @@ struct Coll {
 // antisymmetric non-equilibrium first moment (N_y1 - N_x2)^neq =
 // -(tau_m/3) j_z gives |j|; tau_m = (tau_eta + sqrt(tau_eta^2 +
 // 36 C_S Delta^2 J)) / 2 with J = |N_y1 - N_x2 - 2E|.  g <- g - (g - g^eq)/tau_m.
-template <class R>
+//
+// SCALED: d and g hold s times the deviations (FP16 storage scale s).  Every
+// linear step is unchanged; the four quadratic terms get one factor 1/s,
+// the density needs the unscaled sum, and 18 C_S Delta^2, 36 C_S Delta^2
+// arrive divided by s (Q and J are scaled).  The outputs stay scaled.
+template <class R, bool SCALED = false>
 __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c) {
-    const R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    const R rho = R(1) + drho;
+    const R rho = R(1) + (SCALED ? dsum9 * c.inv_s : dsum9);
     const R irho = rcp(rho);
     const R ux = jx * irho, uy = jy * irho;
     const R bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
@@ -129,16 +140,24 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c)
     const R m7 = R(4) * d[0] - R(5) * ((d[1] + d[2]) + (d[3] + d[4])) + R(4) * dsum;
     const R m8 = R(4) * d[0] - dsum;
 
-    const R j2i = (jx * jx + jy * jy) * irho;
-    const R n3 = m3 - (jx * jy * irho - bx * by);
-    const R n4 = m4 - ((jx * jx - jy * jy) * irho - bx * bx + by * by);
+    R j2i = (jx * jx + jy * jy) * irho;
+    R q3 = jx * jy * irho - bx * by;
+    R q4 = (jx * jx - jy * jy) * irho - bx * bx + by * by;
+    // Ny1 = sum_k C_kx g_ky, Nx2 = sum_k C_ky g_kx; Ny1^eq = E = -Nx2^eq
+    R E = ux * by - uy * bx;
+    if (SCALED) {
+        j2i *= c.inv_s;
+        q3 *= c.inv_s;
+        q4 *= c.inv_s;
+        E *= c.inv_s;
+    }
+    const R n3 = m3 - q3;
+    const R n4 = m4 - q4;
     const R n5 = m5 + jx;
     const R n6 = m6 + jy;
     const R n7 = m7 + R(3) * j2i;
-    const R n8 = m8 - (R(5) / R(3) * drho - R(3) * j2i);
+    const R n8 = m8 - (R(5) / R(3) * dsum9 - R(3) * j2i);
 
-    // Ny1 = sum_k C_kx g_ky, Nx2 = sum_k C_ky g_kx; Ny1^eq = E = -Nx2^eq
-    const R E = ux * by - uy * bx;
     R tau_e = c.tn, tau_m = c.te;
     if (c.les) {
         const R Q = sqrt_(n4 * n4 + R(4) * (n3 * n3));

@@ -230,17 +230,19 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     h->d_flag = (int*)mem[4];
     cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
     // Default launch shape, measured on GB300 at 8192^2: four nodes per
-    // thread in 64-thread blocks for FP32/FP16 storage (FP32: 46.0K MLUPS,
-    // 1.03x the measured copy bandwidth), two nodes in 128-thread blocks for
-    // FP64 (ALU-bound); narrower vectors when nx is not a multiple.
-    const int want = p->precision == LBMHD_FP64 ? 2 : 4;
+    // thread in 64-thread blocks for FP32 storage (46.0K MLUPS, 1.03x the
+    // measured copy bandwidth), eight nodes (16-byte loads) in 32-thread
+    // blocks for FP16 storage (82.0K MLUPS, 0.92x), two nodes in 128-thread
+    // blocks for FP64 (FP64-pipe bound); narrower vectors when nx is not a
+    // multiple.
+    const int want = p->precision == LBMHD_FP64 ? 2 : (p->precision == LBMHD_FP16_DEV ? 8 : 4);
     h->vec = 1;
     for (int v = want; v > 1; v >>= 1)
         if (nx % v == 0) {
             h->vec = v;
             break;
         }
-    h->block = h->vec == 4 ? 64 : 128;
+    h->block = h->vec == 8 ? 32 : (h->vec == 4 ? 64 : 128);
     h->tma_w = 0;
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess ||
@@ -261,7 +263,8 @@ int lbmhd_set_launch(lbmhd_t* h, int vec, int block) {
         h->tma_w = block;
     } else {
         if (!step_variant_ok(h->p.precision, vec, h->geom.nx))
-            return fail(LBMHD_EINVAL, "vector width must be 1, 2 or 4 and divide nx");
+            return fail(LBMHD_EINVAL,
+                        "vector width must be 1, 2, 4 (or 8 for FP16 storage) and divide nx");
         if (block < 32 || block > 256 || block % 32)
             return fail(LBMHD_EINVAL, "block must be a multiple of 32 in [32, 256]");
         h->vec = vec;

@@ -22,11 +22,6 @@ __global__ void __launch_bounds__(256) step_kernel(const typename Fmt<P>::S* __r
         step_body<P, V>(src, dst, nx, ny, ps, t, total, c, scale, inv_scale);
 }
 
-template <class R>
-static Coll<R> to_coll(const HostColl& h) {
-    return make_coll_t<R>(h.tn, h.te, h.k18, h.k36, h.s5, h.s6, h.s7, h.s8, h.les);
-}
-
 template <int P, int V>
 static cudaError_t launch_pv(int block, int max_blocks, const void* src, void* dst, const Geom& g,
                              const HostColl& hc, cudaStream_t st) {
@@ -37,14 +32,14 @@ static cudaError_t launch_pv(int block, int max_blocks, const void* src, void* d
     long long blocks = ((long long)total_pad + block - 1) / block;
     if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
     step_kernel<P, V><<<(unsigned)blocks, block, 0, st>>>(
-        (const S*)src, (S*)dst, g.nx, g.ny, g.ps, total, total_pad, to_coll<R>(hc), hc.scale,
+        (const S*)src, (S*)dst, g.nx, g.ny, g.ps, total, total_pad, coll_for_prec<R>(hc, P), hc.scale,
         hc.inv_scale);
     return cudaGetLastError();
 }
 
 bool step_variant_ok(int prec, int vec, int nx) {
     if (prec < 0 || prec > 3) return false;
-    if (vec != 1 && vec != 2 && vec != 4) return false;
+    if (vec != 1 && vec != 2 && vec != 4 && !(vec == 8 && prec == P_FP16_DEV)) return false;
     return nx % vec == 0;
 }
 
@@ -62,7 +57,14 @@ cudaError_t launch_step(int prec, int vec, int block, int max_blocks, const void
         LBMHD_CASE(P_FP64)
         LBMHD_CASE(P_FP32)
         LBMHD_CASE(P_FP32_DEV)
-        LBMHD_CASE(P_FP16_DEV)
+        case P_FP16_DEV:
+            switch (vec) {
+                case 1: return launch_pv<P_FP16_DEV, 1>(block, max_blocks, src, dst, g, c, st);
+                case 2: return launch_pv<P_FP16_DEV, 2>(block, max_blocks, src, dst, g, c, st);
+                case 4: return launch_pv<P_FP16_DEV, 4>(block, max_blocks, src, dst, g, c, st);
+                case 8: return launch_pv<P_FP16_DEV, 8>(block, max_blocks, src, dst, g, c, st);
+            }
+            break;
     }
 #undef LBMHD_CASE
     return cudaErrorInvalidValue;

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "lbmhd_device.cuh"
+#include "lbmhd_internal.h"
 
 namespace lbmhd {
 
@@ -38,6 +39,91 @@ __device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
     return (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)v, 1);
 }
 
+// FP16 storage with V = 2W nodes per thread: each plane row segment is W
+// 32-bit words, two binary16 values per word (lower address in the low
+// half).  The x-shift of a plane is a funnel of half-words (byte_perm), the
+// two nodes of a word are decoded with one paired conversion and encoded
+// with one (cvt.rn.f16x2.f32), and the collision runs on the scaled values.
+template <int V>
+__device__ __forceinline__ void step_body_h(const unsigned short* __restrict__ src,
+                                            unsigned short* __restrict__ dst, int nx, int ny,
+                                            long long ps, unsigned t, unsigned total,
+                                            const Coll<float>& c) {
+    constexpr int W = V / 2;
+    using Word = unsigned int;
+    const int lane = threadIdx.x & 31;
+    const unsigned nxv = (unsigned)(nx / V);
+    const bool live = t < total;
+    const unsigned tc = live ? t : total - 1;
+    const int y = (int)(tc / nxv);
+    const int x0 = (int)(tc - (unsigned)y * nxv) * V;
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const bool has_left = lane > 0 && x0 > 0;
+    const bool has_right = lane < 31 && x0 + V < nx;
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xr = x0 + V == nx ? 0 : x0 + V;
+
+    Word raw[kPlanes][W];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int cx = plane_cx(p), cy = plane_cy(p);
+        const int row = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const unsigned short* base = src + p * ps + (long long)row * nx;
+        const Pack<Word, W> pk = *reinterpret_cast<const Pack<Word, W>*>(base + x0);
+        if (cx == 0) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) raw[p][j] = pk.v[j];
+        } else if (cx > 0) {  // node x0 - 1 in the high half of the left word
+            Word prev = __shfl_up_sync(0xffffffffu, pk.v[W - 1], 1);
+            if (!has_left) prev = (Word)base[xl] << 16;
+            raw[p][0] = __byte_perm(prev, pk.v[0], 0x5432);
+#pragma unroll
+            for (int j = 1; j < W; ++j) raw[p][j] = __byte_perm(pk.v[j - 1], pk.v[j], 0x5432);
+        } else {  // node x0 + V in the low half of the right word
+            Word next = __shfl_down_sync(0xffffffffu, pk.v[0], 1);
+            if (!has_right) next = (Word)base[xr];
+#pragma unroll
+            for (int j = 0; j < W - 1; ++j) raw[p][j] = __byte_perm(pk.v[j], pk.v[j + 1], 0x5432);
+            raw[p][W - 1] = __byte_perm(pk.v[W - 1], next, 0x5432);
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        float d0[9], g0[10], d1[9], g1[10];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&raw[p][j]));
+            if (p < 9) {
+                d0[p] = f2.x;
+                d1[p] = f2.y;
+            } else {
+                g0[p - 9] = f2.x;
+                g1[p - 9] = f2.y;
+            }
+        }
+        collide<float, true>(d0, g0, c);
+        collide<float, true>(d1, g1, c);
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const __half2 h = p < 9 ? __floats2half2_rn(d0[p], d1[p])
+                                    : __floats2half2_rn(g0[p - 9], g1[p - 9]);
+            raw[p][j] = *reinterpret_cast<const Word*>(&h);
+        }
+    }
+
+    if (live) {
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            Pack<Word, W> o;
+#pragma unroll
+            for (int j = 0; j < W; ++j) o.v[j] = raw[p][j];
+            *reinterpret_cast<Pack<Word, W>*>(dst + p * ps + (long long)y * nx + x0) = o;
+        }
+    }
+}
+
 // One thread's step.  All 32 lanes of the warp must call it together
 // (shuffles); t >= total marks a padding thread, which loads valid
 // addresses (those of thread total - 1) and stores nothing.
@@ -47,6 +133,10 @@ __device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__
                                           long long ps, unsigned t, unsigned total,
                                           const Coll<typename Fmt<P>::R>& c, float scale,
                                           float inv_scale) {
+    if constexpr (P == P_FP16_DEV && V % 2 == 0) {
+        step_body_h<V>(src, dst, nx, ny, ps, t, total, c);
+        return;
+    }
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
     const int lane = threadIdx.x & 31;
@@ -94,7 +184,7 @@ __device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__
         for (int i = 0; i < 9; ++i) d[i] = Fmt<P>::dec(raw[i][k], i, inv_scale);
 #pragma unroll
         for (int q = 0; q < 10; ++q) g[q] = Fmt<P>::dec(raw[9 + q][k], 9 + q, inv_scale);
-        collide<R>(d, g, c);
+        collide<R, Fmt<P>::kScaled>(d, g, c);
 #pragma unroll
         for (int i = 0; i < 9; ++i) raw[i][k] = Fmt<P>::enc(d[i], i, scale);
 #pragma unroll
@@ -130,6 +220,22 @@ __host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18,
     c.les = les;
     c.tie5 = tie5;
     c.tie6 = tie6;
+    c.inv_s = R(1);
+    return c;
+}
+
+// Collision parameters of a storage format: FP16 deviations keep their
+// storage scale through the collision, so the LES constants are divided by
+// it (see collide<R, true>).
+template <class R>
+inline Coll<R> coll_for_prec(const HostColl& h, int prec) {
+    Coll<R> c = make_coll_t<R>(h.tn, h.te, h.k18, h.k36, h.s5, h.s6, h.s7, h.s8, h.les, h.tie5,
+                               h.tie6);
+    if (prec == P_FP16_DEV) {
+        c.k18 = (R)(h.k18 / (double)h.scale);
+        c.k36 = (R)(h.k36 / (double)h.scale);
+        c.inv_s = (R)h.inv_scale;
+    }
     return c;
 }
 

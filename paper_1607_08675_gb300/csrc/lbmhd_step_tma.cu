@@ -24,8 +24,8 @@
 // and returns.
 #include <cuda_fp16.h>
 
-#include "lbmhd_device.cuh"
 #include "lbmhd_internal.h"
+#include "lbmhd_step_body.cuh"
 
 namespace lbmhd {
 
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(W) step_tma_kernel(const typename Fmt<P>::S* _
                                      blockIdx.x + issued * gridDim.x, tiles_x, nx, ny, ps);
             ++issued;
         }
-        collide<R>(d, g, c);
+        collide<R, Fmt<P>::kScaled>(d, g, c);
         S* out = dst + (long long)y * nx + x0 + tid;
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i * ps] = Fmt<P>::enc(d[i], i, scale);
@@ -234,23 +234,6 @@ static cudaError_t launch_tma_pws(const void* src, void* dst, const Geom& g, con
     return cudaGetLastError();
 }
 
-template <class R>
-static Coll<R> coll_of(const HostColl& h) {
-    Coll<R> c;
-    c.tn = (R)h.tn;
-    c.te = (R)h.te;
-    c.tn2 = (R)(h.tn * h.tn);
-    c.te2 = (R)(h.te * h.te);
-    c.k18 = (R)h.k18;
-    c.k36 = (R)h.k36;
-    c.s5 = (R)h.s5;
-    c.s6 = (R)h.s6;
-    c.s7 = (R)h.s7;
-    c.s8 = (R)h.s8;
-    c.les = h.les;
-    return c;
-}
-
 // Tile widths offered: W threads per CTA = nodes per tile.  Stages fill
 // about 160 KB of shared memory.
 bool tma_variant_ok(int prec, int W, int nx) {
@@ -262,7 +245,7 @@ bool tma_variant_ok(int prec, int W, int nx) {
 
 cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
                             const HostColl& hc, int* status, cudaStream_t st) {
-    const Coll<float> c = coll_of<float>(hc);
+    const Coll<float> c = coll_for_prec<float>(hc, prec);
 #define LBMHD_TMA(P, WW, SS) \
     return launch_tma_pws<P, WW, SS>(src, dst, g, c, hc.scale, hc.inv_scale, status, grid, st)
     switch (prec) {
