@@ -188,6 +188,15 @@ def lbmhd_moments(h: Handle):
     return tuple(out)
 
 
+def lbmhd_moments_into(h: Handle, rho, ux, uy, bx, by):
+    """lbmhd_moments into caller-provided float64 arrays (e.g. pinned)."""
+    arrs = [rho, ux, uy, bx, by]
+    for a in arrs:
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.shape != h.shape:
+            raise ValueError(f"expected C-contiguous float64 arrays of shape {h.shape}")
+    _check(lib().lbmhd_moments(h.ptr, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs]))
+
+
 def lbmhd_moments_device(h: Handle, rho, ux, uy, bx, by):
     _check(lib().lbmhd_moments_device(h.ptr, *[_dev(t, h.shape) for t in (rho, ux, uy, bx, by)]))
 
