@@ -38,6 +38,15 @@
  *     implicit dependence on tau is solved exactly (a quadratic in tau).
  *   - s_5, s_6 default to the base 1/tau_nu, s_7 = s_8 to the local s_nu; any
  *     positive value given overrides (the paper leaves them free, Sec. 3).
+ *   - les = 2 is the paper's own kinetic LES (Sec. 4.1): the collision
+ *     relaxes towards the filtered equilibria M_i^eq + Delta^2 M_i^(Delta),
+ *     with M_i^(Delta) obtained by applying the filter rules for products
+ *     (Eq. FilterExampleSmall) and ratios (Eq. FilterExampleLarge) to every
+ *     term of Eqs. KinMomentEq and MagMomentEq (Eq. DeltaEqEx is the M_3
+ *     case the paper prints; the others "are done similarly").  The fields
+ *     in those rules are the resolved conserved moments of the streamed
+ *     populations; their gradients are periodic central differences.  The
+ *     local Smagorinsky rates of les = 1 are not applied in this mode.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -184,13 +193,27 @@ void orc_geq(double ux, double uy, double bx, double by, double* g) {
  * out: the 19 post-collision populations.
  * aux (optional, 4 doubles): tau_nu_eff, tau_m_eff, Q, J.
  */
+static void collide_impl(const double* z, const double* p, const double* shift, double* out,
+                         double* aux);
+
 void orc_collide_cell(const double* z, const double* p, double* out, double* aux) {
+    collide_impl(z, p, NULL, out, aux);
+}
+
+/* As orc_collide_cell, relaxing towards the filtered equilibria shifted by
+ * shift = Delta^2 (M3, M4, M7 = M8, N_y1) corrections (les = 2). */
+void orc_collide_cell_shift(const double* z, const double* p, const double* shift, double* out) {
+    collide_impl(z, p, shift, out, NULL);
+}
+
+static void collide_impl(const double* z, const double* p, const double* shift, double* out,
+                         double* aux) {
     setup();
     const double* f = z;
     const double* g = z + NF;
     double tau_nu = p[P_TAU_NU], tau_eta = p[P_TAU_ETA];
     double CS = p[P_CS], delta = p[P_DELTA];
-    int les = p[P_LES] != 0.0;
+    int les = p[P_LES] == 1.0;
 
     /* moments rho, rho u, B (Sec. 3) */
     double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -220,6 +243,12 @@ void orc_collide_cell(const double* z, const double* p, double* out, double* aux
     Meq[6] = -jy;
     Meq[7] = -3.0 * (jx * jx + jy * jy) / rho;
     Meq[8] = 5.0 / 3.0 * rho - 3.0 * (jx * jx + jy * jy) / rho;
+    if (shift) { /* filtered equilibria (les = 2) */
+        Meq[3] += shift[0];
+        Meq[4] += shift[1];
+        Meq[7] += shift[2];
+        Meq[8] += shift[2];
+    }
 
     double n[NF];
     for (int j = 0; j < NF; ++j) n[j] = M[j] - Meq[j];
@@ -267,10 +296,57 @@ void orc_collide_cell(const double* z, const double* p, double* out, double* aux
     /* magnetic SRT collision in distribution space (Eq. LBMagEqn) */
     double geq[2 * NG];
     orc_geq(ux, uy, bx, by, geq);
+    if (shift) {
+        /* N_y1^eq -> N_y1^eq + D and N_x2^eq -> N_x2^eq - D enter g^eq through
+         * its first-moment term 3 w'_k C_kb (u_b B_a - B_b u_a) */
+        for (int k = 0; k < NG; ++k) {
+            geq[2 * k + 1] += 3.0 * w5(k) * MCX[k] * shift[3];
+            geq[2 * k] -= 3.0 * w5(k) * MCY[k] * shift[3];
+        }
+    }
     double sm = 1.0 / tau_m;
     for (int q = 0; q < 2 * NG; ++q) out[NF + q] = g[q] - sm * (g[q] - geq[q]);
 
     if (aux) { aux[0] = tau_e; aux[1] = tau_m; aux[2] = Q; aux[3] = J; }
+}
+
+/* ---- the paper's kinetic LES (les = 2) ------------------------------------
+ * Filter rules of Sec. 2, summed over the direction beta:
+ *   product (Eq. FilterExampleSmall):  P(X, Y) = (1/12) dX . dY
+ *   ratio   (Eq. FilterExampleLarge):  Rt(X, Y; Z) = 1/(12 Z) [ dX . dY
+ *            - (X dZ . dY + Y dZ . dX - X Y dZ . dZ / Z) / Z ]
+ * The filtered equilibrium of a term XY (XY/Z) is its value in the filtered
+ * fields plus Delta^2 P (Delta^2 Rt).  Applied to Eq. KinMomentEq (linear
+ * terms have no correction):
+ *   M3: Rt(jx, jy; rho) - P(Bx, By)
+ *   M4: Rt(jx, jx; rho) - Rt(jy, jy; rho) - P(Bx, Bx) + P(By, By)
+ *   M7 = M8: -3 (Rt(jx, jx; rho) + Rt(jy, jy; rho))
+ * and to Eq. MagMomentEq with u (reading above), N_y1^eq = (jx By - jy Bx)/rho
+ * = -N_x2^eq:
+ *   N_y1: Rt(jx, By; rho) - Rt(jy, Bx; rho),  N_x2 the negative.
+ * d[q][a]: derivative of field q (rho, jx, jy, Bx, By) along a (x, y).
+ * out: Delta^2 times (M3, M4, M7 (= M8), N_y1) corrections. */
+static double dotg(const double d[5][2], int a, int b) {
+    return d[a][0] * d[b][0] + d[a][1] * d[b][1];
+}
+
+static double rt(double X, double Y, double Z, int ix, int iy, int iz, const double d[5][2]) {
+    return (dotg(d, ix, iy) - (X * dotg(d, iz, iy) + Y * dotg(d, iz, ix) - X * Y * dotg(d, iz, iz) / Z) / Z) /
+           (12.0 * Z);
+}
+
+void orc_kinetic_shift(const double* fld, const double* grad, double delta, double* out) {
+    double d[5][2];
+    for (int q = 0; q < 5; ++q) { d[q][0] = grad[2 * q]; d[q][1] = grad[2 * q + 1]; }
+    double rho = fld[0], jx = fld[1], jy = fld[2], bx = fld[3], by = fld[4];
+    double d2 = delta * delta;
+    double Rxx = rt(jx, jx, rho, 1, 1, 0, d), Ryy = rt(jy, jy, rho, 2, 2, 0, d);
+    double Rxy = rt(jx, jy, rho, 1, 2, 0, d);
+    double Pxy = dotg(d, 3, 4) / 12.0, Pxx = dotg(d, 3, 3) / 12.0, Pyy = dotg(d, 4, 4) / 12.0;
+    out[0] = d2 * (Rxy - Pxy);
+    out[1] = d2 * (Rxx - Ryy - Pxx + Pyy);
+    out[2] = d2 * (-3.0 * (Rxx + Ryy));
+    out[3] = d2 * (rt(jx, by, rho, 1, 4, 0, d) - rt(jy, bx, rho, 2, 3, 0, d));
 }
 
 /* ---- lattice-wide operations --------------------------------------------- */
@@ -312,6 +388,9 @@ void orc_init(int nx, int ny, const double* rho, const double* ux, const double*
  * state (19 planes) is advanced in place; work is a caller buffer of the
  * same size.  nthreads > 1 splits the collision loop over rows (OpenMP
  * builds only); results do not depend on it. */
+static void kinetic_collide_all(int nx, int ny, const double* p, const double* work,
+                                double* state);
+
 int orc_step(int nx, int ny, const double* p, double* state, double* work, int nsteps,
              int nthreads) {
     setup();
@@ -319,6 +398,10 @@ int orc_step(int nx, int ny, const double* p, double* state, double* work, int n
     (void)nthreads;
     for (int t = 0; t < nsteps; ++t) {
         orc_stream(nx, ny, state, work);
+        if (p[P_LES] == 2.0) {
+            kinetic_collide_all(nx, ny, p, work, state);
+            continue;
+        }
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
 #endif
@@ -335,8 +418,60 @@ int orc_step(int nx, int ny, const double* p, double* state, double* work, int n
     return 0;
 }
 
+/* les = 2: conserved moments of the streamed populations, their periodic
+ * central differences, the filtered-equilibrium shifts, then the collision. */
+static void kinetic_collide_all(int nx, int ny, const double* p, const double* work,
+                                double* state) {
+    long N = (long)nx * ny;
+    double* m = (double*)malloc(sizeof(double) * 5 * N);
+    for (long c = 0; c < N; ++c) {
+        double r = 0, jx = 0, jy = 0, bx = 0, by = 0;
+        for (int i = 0; i < NF; ++i) {
+            double fi = work[i * N + c];
+            r += fi; jx += CX[i] * fi; jy += CY[i] * fi;
+        }
+        for (int k = 0; k < NG; ++k) {
+            bx += work[(NF + 2 * k) * N + c];
+            by += work[(NF + 2 * k + 1) * N + c];
+        }
+        m[c] = r; m[N + c] = jx; m[2 * N + c] = jy; m[3 * N + c] = bx; m[4 * N + c] = by;
+    }
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            long c = y * nx + x;
+            long xp = y * nx + wrap(x + 1, nx), xm = y * nx + wrap(x - 1, nx);
+            long yp = wrap(y + 1, ny) * nx + x, ym = wrap(y - 1, ny) * nx + x;
+            double fld[5], grad[10], z[NPLANE], o[NPLANE], sh[4];
+            for (int q = 0; q < 5; ++q) {
+                fld[q] = m[q * N + c];
+                grad[2 * q] = 0.5 * (m[q * N + xp] - m[q * N + xm]);
+                grad[2 * q + 1] = 0.5 * (m[q * N + yp] - m[q * N + ym]);
+            }
+            orc_kinetic_shift(fld, grad, p[P_DELTA], sh);
+            for (int q = 0; q < NPLANE; ++q) z[q] = work[q * N + c];
+            collide_impl(z, p, sh, o, NULL);
+            for (int q = 0; q < NPLANE; ++q) state[q * N + c] = o[q];
+        }
+    free(m);
+}
+
 /* One step evaluated at selected nodes only: out[c*19 + q] is the
  * post-collision population q at node idx[c] after streaming from state. */
+/* Conserved moments (rho, jx, jy, Bx, By) of the populations streamed into
+ * node (x, y). */
+static void streamed_moments(int nx, int ny, const double* state, long x, long y, double* m) {
+    long N = (long)nx * ny;
+    x = wrap(x, nx);
+    y = wrap(y, ny);
+    for (int q = 0; q < 5; ++q) m[q] = 0.0;
+    for (int p = 0; p < NPLANE; ++p) {
+        double v = state[p * N + wrap(y - plane_cy(p), ny) * nx + wrap(x - plane_cx(p), nx)];
+        if (p < NF) { m[0] += v; m[1] += CX[p] * v; m[2] += CY[p] * v; }
+        else if ((p - NF) % 2 == 0) m[3] += v;
+        else m[4] += v;
+    }
+}
+
 void orc_step_cells(int nx, int ny, const double* p, const double* state, long ncells,
                     const long* idx, double* out) {
     setup();
@@ -346,7 +481,22 @@ void orc_step_cells(int nx, int ny, const double* p, const double* state, long n
         double z[NPLANE];
         for (int q = 0; q < NPLANE; ++q)
             z[q] = state[q * N + wrap(y - plane_cy(q), ny) * nx + wrap(x - plane_cx(q), nx)];
-        orc_collide_cell(z, p, out + c * NPLANE, NULL);
+        if (p[P_LES] == 2.0) {
+            double m0[5], mxp[5], mxm[5], myp[5], mym[5], grad[10], sh[4];
+            streamed_moments(nx, ny, state, x, y, m0);
+            streamed_moments(nx, ny, state, x + 1, y, mxp);
+            streamed_moments(nx, ny, state, x - 1, y, mxm);
+            streamed_moments(nx, ny, state, x, y + 1, myp);
+            streamed_moments(nx, ny, state, x, y - 1, mym);
+            for (int q = 0; q < 5; ++q) {
+                grad[2 * q] = 0.5 * (mxp[q] - mxm[q]);
+                grad[2 * q + 1] = 0.5 * (myp[q] - mym[q]);
+            }
+            orc_kinetic_shift(m0, grad, p[P_DELTA], sh);
+            collide_impl(z, p, sh, out + c * NPLANE, NULL);
+        } else {
+            orc_collide_cell(z, p, out + c * NPLANE, NULL);
+        }
     }
 }
 

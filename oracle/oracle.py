@@ -70,6 +70,8 @@ def _load():
             "orc_moments": (None, [i32, i32, dp, dp, dp, dp, dp, dp]),
             "orc_diagnostics": (None, [i32, i32, dp, dp]),
             "orc_step_bgk": (i32, [i32, i32, d, d, dp, dp, i32]),
+            "orc_kinetic_shift": (None, [dp, dp, d, dp]),
+            "orc_collide_cell_shift": (None, [dp, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -86,7 +88,8 @@ def _dp(a: np.ndarray):
 
 def params(tau_nu=0.6, tau_eta=0.6, C_S=0.1, delta=1.0, s5=0.0, s6=0.0, s7=0.0, s8=0.0, les=1):
     """Parameter dict; s5..s8 <= 0 means tied (s5, s6 to 1/tau_nu; s7, s8 to
-    the local s_nu)."""
+    the local s_nu).  les: 0 none, 1 local Smagorinsky rates, 2 the paper's
+    filtered equilibria (kinetic LES)."""
     return dict(tau_nu=tau_nu, tau_eta=tau_eta, C_S=C_S, delta=delta, s5=s5, s6=s6, s7=s7,
                 s8=s8, les=les)
 
@@ -134,6 +137,25 @@ def collide_cell(z: np.ndarray, p: dict):
     out, aux = np.zeros(19), np.zeros(4)
     _load().orc_collide_cell(_dp(z), _dp(_pvec(p)), _dp(out), _dp(aux))
     return out, aux
+
+
+def kinetic_shift(fields, grads, delta=1.0) -> np.ndarray:
+    """Delta^2 times the filtered-equilibrium corrections (M3, M4, M7 = M8,
+    N_y1) at one node; fields = (rho, jx, jy, Bx, By), grads[q] = (d/dx,
+    d/dy) of field q."""
+    f = np.ascontiguousarray(fields, dtype=np.float64)
+    g = np.ascontiguousarray(np.asarray(grads, dtype=np.float64).reshape(10))
+    out = np.zeros(4)
+    _load().orc_kinetic_shift(_dp(f), _dp(g), float(delta), _dp(out))
+    return out
+
+
+def collide_cell_shift(z: np.ndarray, p: dict, shift) -> np.ndarray:
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    sh = np.ascontiguousarray(shift, dtype=np.float64)
+    out = np.zeros(19)
+    _load().orc_collide_cell_shift(_dp(z), _dp(_pvec(p)), _dp(sh), _dp(out))
+    return out
 
 
 def init(rho, ux, uy, bx, by) -> np.ndarray:

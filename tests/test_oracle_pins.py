@@ -517,3 +517,168 @@ def test_step_cells_matches_full_step(orc):
     idx = np.array([0, 5, 10, 11, 40, 76])
     got = orc.step_cells(st, p, idx)
     assert np.array_equal(got, full.reshape(19, -1)[:, idx].T)
+
+
+# ---------------------------------------------------------------- the paper's kinetic LES (les = 2)
+
+
+def test_kinetic_shift_m3_is_the_printed_delta_equation(orc):
+    """Eq. DeltaEqEx prints Delta^2 M_3^(Delta); the oracle builds every
+    shift from the filter rules, and its M_3 entry must be that equation."""
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        rho = rng.uniform(0.8, 1.2)
+        jx, jy, bx, by = rng.uniform(-0.1, 0.1, 4)
+        gr = rng.uniform(-0.01, 0.01, (5, 2))
+        delta = rng.uniform(0.5, 3.0)
+        sh = orc.kinetic_shift([rho, jx, jy, bx, by], gr, delta)
+        dr, djx, djy, dbx, dby = gr
+        dot = lambda a, b: a @ b
+        printed = (delta ** 2 / (12 * rho) * (dot(djx, djy) - (dr / rho) @ (jx * djy + jy * djx
+                                                                              - jx * jy * dr / rho))
+                   - delta ** 2 / 12 * dot(dbx, dby))
+        assert abs(sh[0] - printed) < 1e-15 * max(1.0, abs(printed))
+
+
+def _gauss_filter_1d(f, x, delta):
+    """The Gaussian filter of Eq. Gaussian (1D factor), by quadrature on a
+    periodic grid of spacing h: Xbar(x) = sum_r X(x - r) G(r) h."""
+    h = x[1] - x[0]
+    r = np.arange(-len(x) // 2, len(x) // 2) * h
+    G = np.sqrt(6.0 / (np.pi * delta ** 2)) * np.exp(-6.0 * r ** 2 / delta ** 2)
+    out = np.zeros_like(f)
+    for j, rj in enumerate(r):
+        out += np.roll(f, int(round(rj / h))) * G[j] * h
+    return out
+
+
+@pytest.mark.parametrize("which", ["product", "ratio"])
+def test_filter_rules_match_gaussian_filtering(orc, which):
+    """Eqs. FilterExampleSmall / FilterExampleLarge against brute-force
+    filtering with the paper's Gaussian: the error of the rule falls as
+    Delta^4 (the order the paper truncates at)."""
+    L = 2 * np.pi
+    x = np.linspace(0, L, 4096, endpoint=False)
+    X = 0.3 + 0.2 * np.sin(x) + 0.1 * np.cos(2 * x)
+    Y = 0.1 * np.cos(x) - 0.2 * np.sin(3 * x)
+    Z = 1.0 + 0.2 * np.sin(x + 0.3)
+    k = np.fft.fftfreq(len(x), L / len(x)) * 2 * np.pi
+    deriv = lambda f: np.real(np.fft.ifft(1j * k * np.fft.fft(f)))
+    errs, plain = [], []
+    for delta in (0.2, 0.1):
+        Xb, Yb, Zb = (_gauss_filter_1d(a, x, delta) for a in (X, Y, Z))
+        if which == "product":
+            exact = _gauss_filter_1d(X * Y, x, delta)
+            # P(Bx, By) is -shift[0] with no momentum
+            rule = np.array([Xb[i] * Yb[i] - orc.kinetic_shift(
+                [1.0, 0, 0, Xb[i], Yb[i]],
+                [[0, 0], [0, 0], [0, 0], [deriv(Xb)[i], 0], [deriv(Yb)[i], 0]], delta)[0]
+                for i in range(0, len(x), 64)])
+        else:
+            exact = _gauss_filter_1d(X * X / Z, x, delta)
+            # Rt(jx, jx; rho) is -shift[2] / 3 with jy = B = 0
+            rule = np.array([Xb[i] * Xb[i] / Zb[i] - orc.kinetic_shift(
+                [Zb[i], Xb[i], 0, 0, 0],
+                [[deriv(Zb)[i], 0], [deriv(Xb)[i], 0], [0, 0], [0, 0], [0, 0]], delta)[2] / 3.0
+                for i in range(0, len(x), 64)])
+        errs.append(np.max(np.abs(rule - exact[::64])))
+        unfiltered = (Xb * Yb if which == "product" else Xb * Xb / Zb)[::64]
+        plain.append(np.max(np.abs(unfiltered - exact[::64])))
+    assert errs[1] < 1e-6
+    assert 10.0 < errs[0] / errs[1] < 24.0  # fourth order
+    assert plain[1] > 100 * errs[1]  # without the Delta^2 term: second order only
+
+
+def test_kinetic_les_vanishing_width_is_les_off(orc):
+    st = _noneq_state(orc, 10, 8, 3)
+    a = orc.step(st, orc.params(les=2, delta=1e-200), 6)
+    b = orc.step(st, orc.params(les=0), 6)
+    assert np.array_equal(a, b)
+
+
+def test_kinetic_les_conserves_and_step_cells_agree(orc):
+    st = orc.init(*inputs.orszag_tang(24, 20, seed=6))
+    p = orc.params(tau_nu=0.6, tau_eta=0.65, les=2, delta=3.0)
+    d0 = orc.diagnostics(st)
+    s1 = orc.step(st, p, 100)
+    d1 = orc.diagnostics(s1)
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    for k in ("mom_x", "mom_y", "bsum_x", "bsum_y"):
+        assert abs(d1[k] - d0[k]) < 1e-13 * d0["mass"]
+    idx = np.array([0, 23, 24, 200, 479])
+    full = orc.step(s1, p, 1)
+    assert np.array_equal(orc.step_cells(s1, p, idx), full.reshape(19, -1)[:, idx].T)
+
+
+def _kin_pair(orc, n, tau_nu, tau_eta, delta, with_b):
+    x = 2 * np.pi * np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    U = 0.05
+    ux = U * np.sin(Y) + 0.5 * U * np.sin(X + Y)
+    uy = 0.5 * U * np.sin(X) + 0.3 * U * np.cos(2 * Y)
+    bx = 0.05 * np.sin(2 * Y) if with_b else np.zeros_like(ux)
+    by = 0.05 * np.sin(X) if with_b else np.zeros_like(ux)
+    st = orc.init(np.ones_like(ux), ux, uy, bx, by)
+    return (st, orc.params(tau_nu=tau_nu, tau_eta=tau_eta, les=2, delta=delta),
+            orc.params(tau_nu=tau_nu, tau_eta=tau_eta, les=0))
+
+
+def _dlat(f, ax):
+    n = f.shape[0]
+    k = np.fft.fftfreq(n, 1.0 / n) * 2 * np.pi / n
+    kk = k[None, :] if ax == 1 else k[:, None]
+    return np.real(np.fft.ifft2(1j * kk * np.fft.fft2(f)))
+
+
+def test_kinetic_les_vorticity_tendency_is_the_subgrid_force(orc):
+    """The filtered equilibria must add the subgrid force of Eq. FinalMomentum,
+    -div(Delta^2/12 d_b(rho u) d_b(rho u)) for rho ~ 1, to the momentum
+    equation.  Compared through the vorticity tendency (curl removes the
+    sound the force's gradient part radiates), run with les = 2 minus les = 0
+    from the same state.  Measured factor: 1 (the discrete step passes an
+    equilibrium shift at full weight), not the 6 nu/(6 nu + 1) = 0.375 the
+    paper prints at tau = 0.8."""
+    n, delta = 48, 4.0
+    st, pa, pb = _kin_pair(orc, n, 0.8, 0.8, delta, False)
+    sa, sb = st, st
+    prev, ratios = None, []
+    curl = lambda vx, vy: _dlat(vy, 1) - _dlat(vx, 0)
+    for t in range(1, 9):
+        sa, sb = orc.step(sa, pa, 1), orc.step(sb, pb, 1)
+        ma, mb = orc.moments(sa), orc.moments(sb)
+        dj = (ma[0] * ma[1] - mb[0] * mb[1], ma[0] * ma[2] - mb[0] * mb[2])
+        w = curl(*dj)
+        rate, prev = (w - prev if prev is not None else w), w
+        jx, jy = mb[0] * mb[1], mb[0] * mb[2]
+        T = {(a, g): _dlat(ja, 1) * _dlat(jg, 1) + _dlat(ja, 0) * _dlat(jg, 0)
+             for a, ja in (("x", jx), ("y", jy)) for g, jg in (("x", jx), ("y", jy))}
+        Fx = -(delta ** 2 / 12) * (_dlat(T["x", "x"], 1) + _dlat(T["x", "y"], 0))
+        Fy = -(delta ** 2 / 12) * (_dlat(T["y", "x"], 1) + _dlat(T["y", "y"], 0))
+        F = curl(Fx, Fy)
+        if t >= 3:
+            ratios.append(np.sum(rate * F) / np.sum(F * F))
+            assert np.sum(rate * F) / np.sqrt(np.sum(rate ** 2) * np.sum(F ** 2)) > 0.99
+    assert 0.95 < np.mean(ratios) < 1.08, ratios
+
+
+def test_kinetic_les_emf_is_the_subgrid_induction(orc):
+    """The shifted magnetic equilibrium must add curl(D z) to dB/dt with
+    D = Delta^2/12 (d_b(rho u) x d_b B)_z, the subgrid EMF of
+    Eq. FinalMagnetic (rho ~ 1); measured factor 1, as for the momentum."""
+    n, delta = 48, 4.0
+    st, pa, pb = _kin_pair(orc, n, 0.8, 0.8, delta, True)
+    sa, sb = st, st
+    prev, ratios = None, []
+    for t in range(1, 7):
+        sa, sb = orc.step(sa, pa, 1), orc.step(sb, pb, 1)
+        ma, mb = orc.moments(sa), orc.moments(sb)
+        dB = np.stack([ma[3] - mb[3], ma[4] - mb[4]])
+        rate, prev = (dB - prev if prev is not None else dB), dB
+        jx, jy, Bx, By = mb[0] * mb[1], mb[0] * mb[2], mb[3], mb[4]
+        D = delta ** 2 / 12 * (_dlat(jx, 1) * _dlat(By, 1) + _dlat(jx, 0) * _dlat(By, 0)
+                               - _dlat(jy, 1) * _dlat(Bx, 1) - _dlat(jy, 0) * _dlat(Bx, 0))
+        pred = np.stack([_dlat(D, 0), -_dlat(D, 1)])
+        if t >= 3:
+            ratios.append(np.sum(rate * pred) / np.sum(pred * pred))
+            assert np.sum(rate * pred) / np.sqrt(np.sum(rate ** 2) * np.sum(pred ** 2)) > 0.99
+    assert 0.9 < np.mean(ratios) < 1.08, ratios
