@@ -514,6 +514,19 @@ def run_ours(args):
     # ---- other storage forms on the same lattice ---------------------------
     variants = {}
     if not args.no_variants:
+        # the paper's kinetic LES: a moments pass + the step, FP32; algorithmic
+        # bytes per node: 19 reads + 5 writes, 19 + 5 reads + 19 writes
+        hk = L.lbmhd_create(n, n, L.lbmhd_params_default(
+            precision="fp32", **dict(kw, les=2, delta=2.0)))
+        L.lbmhd_init(hk, *fields)
+        barrier()
+        ksteps = max(2, args.steps // 5)
+        t = max_over_ranks(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
+        L.lbmhd_destroy(hk)
+        variants["fp32_kinetic_les"] = {
+            "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps, "bytes_per_cell": 268,
+            "hbm_frac": 268 * cells * ksteps / t / 1e9 / hbm,
+            "note": "les=2 (filtered equilibria, Delta=2): moments pass + step per time step"}
         for vp, vsteps in (("fp64", args.steps // 10), ("fp32_dev", args.steps),
                            ("fp16_dev", args.steps)):
             if vp == prec:

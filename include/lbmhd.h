@@ -30,7 +30,15 @@
  * nu_t = C_S Delta^2 |S| and eta_t = C_S Delta^2 |j| of
  * Eqs. SmagorinskyMHDClosureV/B, with |S| and |j| taken from the node's own
  * non-equilibrium moments (Sec. 1.2: sum c_a c_b f^(1) = -(rho tau/3) 2 S_ab)
- * and the implicit dependence on tau solved exactly.
+ * and the implicit dependence on tau solved exactly.  With les = 2 the
+ * collision instead relaxes towards the paper's filtered equilibria
+ * (Sec. 4.1): M_i^eq + Delta^2 M_i^(Delta), the corrections obtained by
+ * applying the filter rules for products and ratios (Eqs.
+ * FilterExampleSmall/Large) to Eqs. KinMomentEq and MagMomentEq (Eq.
+ * DeltaEqEx is the M_3 case), with periodic central differences of the
+ * streamed conserved moments; each step is then two launches (a moments
+ * pass and the step) and needs 5 extra planes of device memory.  les = 2 is
+ * not available to ensembles or the adjoint.
  */
 #ifndef LBMHD_H
 #define LBMHD_H
@@ -76,7 +84,8 @@ typedef struct {
     double delta;          /* filter width Delta in lattice units, > 0 */
     double s5, s6;         /* energy-flux rates; <= 0: tied to 1/tau_nu */
     double s7, s8;         /* energy rates; <= 0: tied to the local s_nu */
-    int32_t les;           /* 0: no eddy terms; 1: local Smagorinsky rates */
+    int32_t les;           /* 0: none; 1: local Smagorinsky rates; 2: the paper's
+                              filtered equilibria (kinetic LES, see below) */
     int32_t check_finite_every; /* 0: never; k: test rho every k steps */
     double fp16_scale;     /* LBMHD_FP16_DEV: stored = deviation * scale */
     void* stream;          /* cudaStream_t to run on; NULL: library stream */

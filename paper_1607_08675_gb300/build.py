@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liblbmhd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["lbmhd_step.cu", "lbmhd_step_tma.cu", "lbmhd_aux.cu", "lbmhd_runtime.cu", "lbmhd_noalloc.cu",
-           "lbmhd_batch.cu", "lbmhd_adjoint.cu"]
+           "lbmhd_batch.cu", "lbmhd_adjoint.cu", "lbmhd_kinetic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -97,7 +97,35 @@ struct Coll {
     int les;
     int tie5, tie6;  // s5 (s6) is the tied value 1/tau_nu
     R inv_s;         // scaled storage: 1 / scale (k18, k36 already divided by scale)
+    R scl;           // scaled storage: the scale itself (1 otherwise)
+    R d2;            // Delta^2 (filtered equilibria, les = 2)
 };
+
+// Filtered-equilibrium corrections of the paper's kinetic LES (Sec. 4.1):
+// the filter rules for a product XY, (1/12) dX . dY (Eq. FilterExampleSmall),
+// and for a ratio XY/Z, (1/(12 Z)) [dX . dY - (X dZ . dY + Y dZ . dX -
+// X Y dZ . dZ / Z) / Z] (Eq. FilterExampleLarge), applied to the terms of
+// Eqs. KinMomentEq and MagMomentEq.  fld = (rho, jx, jy, Bx, By) at the
+// node, gx / gy their x / y derivatives; returns Delta^2 times the
+// corrections of M_3, M_4, M_7 (= M_8) and N_y1 (= -N_x2).
+template <class R>
+__device__ __forceinline__ void filtered_shift(const R (&fld)[5], const R (&gx)[5],
+                                               const R (&gy)[5], R d2, R (&sh)[4]) {
+    const R rho = fld[0], ir = R(1) / fld[0];
+    auto dot = [&](int a, int b) { return gx[a] * gx[b] + gy[a] * gy[b]; };
+    // ratio rule with Z = rho for fields a, b
+    auto ratio = [&](int a, int b) {
+        return (dot(a, b) - (fld[a] * dot(0, b) + fld[b] * dot(0, a) - fld[a] * fld[b] * dot(0, 0) * ir) * ir) *
+               (ir * (R(1) / R(12)));
+    };
+    const R twelfth = R(1) / R(12);
+    const R rxx = ratio(1, 1), ryy = ratio(2, 2), rxy = ratio(1, 2);
+    (void)rho;
+    sh[0] = d2 * (rxy - twelfth * dot(3, 4));
+    sh[1] = d2 * ((rxx - ryy) - twelfth * (dot(3, 3) - dot(4, 4)));
+    sh[2] = d2 * (R(-3) * (rxx + ryy));
+    sh[3] = d2 * (ratio(1, 4) - ratio(2, 3));
+}
 
 // One node: d[9] = streamed f_i - w_i, g[10] = streamed g_k (x, y);
 // overwritten with the post-collision values.
@@ -121,8 +149,12 @@ struct Coll {
 // linear step is unchanged; the four quadratic terms get one factor 1/s,
 // the density needs the unscaled sum, and 18 C_S Delta^2, 36 C_S Delta^2
 // arrive divided by s (Q and J are scaled).  The outputs stay scaled.
-template <class R, bool SCALED = false>
-__device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c) {
+//
+// KIN: relax towards the filtered equilibria, sh = Delta^2 corrections of
+// M_3, M_4, M_7 = M_8 and N_y1 (in the units of d and g).
+template <class R, bool SCALED = false, bool KIN = false>
+__device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
+                                        const R* sh = nullptr) {
     const R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
@@ -151,12 +183,20 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c)
         q4 *= c.inv_s;
         E *= c.inv_s;
     }
+    R k7 = R(0);
+    if (KIN) {
+        q3 += sh[0];
+        q4 += sh[1];
+        k7 = sh[2];
+        E += sh[3];
+    }
     const R n3 = m3 - q3;
     const R n4 = m4 - q4;
     const R n5 = m5 + jx;
     const R n6 = m6 + jy;
-    const R n7 = m7 + R(3) * j2i;
-    const R n8 = m8 - (R(5) / R(3) * dsum9 - R(3) * j2i);
+    const R n7 = KIN ? (m7 + R(3) * j2i) - k7 : m7 + R(3) * j2i;
+    const R n8 = KIN ? m8 - ((R(5) / R(3) * dsum9 - R(3) * j2i) + k7)
+                     : m8 - (R(5) / R(3) * dsum9 - R(3) * j2i);
 
     R tau_e = c.tn, tau_m = c.te;
     if (c.les) {

@@ -20,6 +20,8 @@ struct HostColl {
     int les;
     float scale, inv_scale;  // FP16_DEV encoding
     int tie5, tie6;          // s5 / s6 are the tied 1/tau_nu
+    int kin;                 // les = 2: filtered equilibria (kinetic LES)
+    double d2;               // Delta^2
 };
 
 // Geometry of one lattice in device memory: 19 planes of ps elements each,
@@ -42,6 +44,12 @@ bool step_variant_ok(int prec, int vec, int nx);
 // TMA-staged step (lbmhd_step_tma.cu): W threads = nodes per row tile,
 // persistent grid of `grid` CTAs; a timed-out wait sets bit 2 of *status.
 bool tma_variant_ok(int prec, int W, int nx);
+
+// Kinetic-LES step (lbmhd_kinetic.cu): conserved moments of the streamed
+// populations into `mom` (5 planes of the arithmetic type, plane stride
+// g.ps), then the step relaxing towards the filtered equilibria.
+cudaError_t launch_step_kinetic(int prec, const void* src, void* dst, void* mom, const Geom& g,
+                                const HostColl& c, cudaStream_t st);
 cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
                             const HostColl& c, int* status, cudaStream_t st);
 
@@ -94,6 +102,7 @@ struct lbmhd_t {
     int64_t steps;
     int64_t launches;
     void* tape;  // adjoint checkpoints (lbmhd_adjoint.cu), NULL when none
+    void* d_kin; // les = 2: streamed conserved moments (5 planes)
     double* d_partials;
     double* d_diag;
     int* d_flag;

@@ -80,7 +80,7 @@ int lbmhd::validate_params(int nx, int ny, const lbmhd_params* p) {
     for (double s : {p->s5, p->s6, p->s7, p->s8})
         if (s > 0.0 && !(s < 2.0)) return fail(LBMHD_EINVAL, "given rates s5..s8 must lie in (0, 2)");
     if (!(p->fp16_scale > 0.0)) return fail(LBMHD_EINVAL, "fp16_scale must be > 0");
-    if (p->les != 0 && p->les != 1) return fail(LBMHD_EINVAL, "les must be 0 or 1");
+    if (p->les < 0 || p->les > 2) return fail(LBMHD_EINVAL, "les must be 0, 1 or 2");
     if (p->check_finite_every < 0) return fail(LBMHD_EINVAL, "check_finite_every must be >= 0");
     // bulk viscosity (Sec. 4.3) at the base rates
     const double s4 = 1.0 / p->tau_nu;
@@ -105,7 +105,9 @@ HostColl make_coll(const lbmhd_params* p) {
     c.tie6 = p->s6 > 0.0 ? 0 : 1;
     c.s7 = p->s7 > 0.0 ? p->s7 : 0.0;
     c.s8 = p->s8 > 0.0 ? p->s8 : 0.0;
-    c.les = p->les;
+    c.les = p->les == 1 ? 1 : 0;
+    c.kin = p->les == 2 ? 1 : 0;
+    c.d2 = p->delta * p->delta;
     c.scale = (float)p->fp16_scale;
     c.inv_scale = (float)(1.0 / p->fp16_scale);
     return c;
@@ -140,6 +142,9 @@ int read_flag(lbmhd_t* h) {
 }
 
 cudaError_t launch_one(lbmhd_t* h, const void* src, void* dst) {
+    if (h->coll.kin)
+        return launch_step_kinetic(h->p.precision, src, dst, h->d_kin, h->geom, h->coll,
+                                   h->stream);
     if (h->tma_w > 0)
         return launch_step_tma(h->p.precision, h->tma_w, h->sm_count, src, dst, h->geom, h->coll,
                                h->d_flag, h->stream);
@@ -150,7 +155,7 @@ cudaError_t one_step(lbmhd_t* h) {
     cudaError_t e = launch_one(h, h->buf[h->cur], h->buf[1 - h->cur]);
     if (e == cudaSuccess) {
         h->cur = 1 - h->cur;
-        ++h->launches;
+        h->launches += h->coll.kin ? 2 : 1;
     }
     return e;
 }
@@ -225,6 +230,17 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     }
     h->buf[0] = mem[0];
     h->buf[1] = mem[1];
+    if (p->les == 2) {
+        const size_t kb = (size_t)5 * h->geom.ps * (p->precision == LBMHD_FP64 ? 8 : 4);
+        e = cudaMalloc(&h->d_kin, kb);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < 5; ++j) cudaFree(mem[j]);
+            if (h->own_stream) cudaStreamDestroy(h->stream);
+            delete h;
+            cudaGetLastError();
+            return fail(LBMHD_ENOMEM, "device allocation failed (filtered-equilibrium moments)");
+        }
+    }
     h->d_partials = (double*)mem[2];
     h->d_diag = (double*)mem[3];
     h->d_flag = (int*)mem[4];
@@ -350,7 +366,7 @@ int lbmhd_step(lbmhd_t* h, int n) {
                 h->graph_steps = kGraphSteps;
             }
             LBMHD_CK(h, cudaGraphLaunch(h->graph, h->stream));
-            h->launches += kGraphSteps;
+            h->launches += kGraphSteps * (h->coll.kin ? 2 : 1);
             done += kGraphSteps;
             h->steps += kGraphSteps;
             continue;
@@ -483,6 +499,7 @@ void lbmhd_destroy(lbmhd_t* h) {
     cudaFree(h->d_partials);
     cudaFree(h->d_diag);
     cudaFree(h->d_flag);
+    cudaFree(h->d_kin);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -221,6 +221,8 @@ __host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18,
     c.tie5 = tie5;
     c.tie6 = tie6;
     c.inv_s = R(1);
+    c.scl = R(1);
+    c.d2 = R(0);
     return c;
 }
 
@@ -231,10 +233,12 @@ template <class R>
 inline Coll<R> coll_for_prec(const HostColl& h, int prec) {
     Coll<R> c = make_coll_t<R>(h.tn, h.te, h.k18, h.k36, h.s5, h.s6, h.s7, h.s8, h.les, h.tie5,
                                h.tie6);
+    c.d2 = (R)h.d2;
     if (prec == P_FP16_DEV) {
         c.k18 = (R)(h.k18 / (double)h.scale);
         c.k36 = (R)(h.k36 / (double)h.scale);
         c.inv_s = (R)h.inv_scale;
+        c.scl = (R)h.scale;
     }
     return c;
 }

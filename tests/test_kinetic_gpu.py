@@ -1,0 +1,126 @@
+"""The paper's kinetic LES (les = 2, filtered equilibria of Sec. 4.1) on the
+GPU against the oracle's les = 2 step.  Bars as in test_parity_gpu: FP64
+1e-12 relative per field after 200 steps; FP32 storage 2e-4; FP32
+deviations 3e-5; FP16 deviations 2e-2 (u, B) and 5e-2 (rho - 1)."""
+import numpy as np
+import pytest
+
+from paper_1607_08675_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho-1", "ux", "uy", "bx", "by")
+KW = dict(tau_nu=0.6, tau_eta=0.65, C_S=0.0, delta=3.0, les=2)
+MRT = dict(s5=1.2, s6=1.25, s7=1.3, s8=1.35)
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_08675_gb300 import build, lbmhd
+
+    build.build()
+    return lbmhd
+
+
+def gpu(L, fields, steps, **kw):
+    ny, nx = fields[0].shape
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(**kw))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, steps)
+    out = L.lbmhd_moments(h), L.lbmhd_get_state(h)
+    L.lbmhd_destroy(h)
+    return out
+
+
+def okw(kw):
+    return {k: v for k, v in kw.items() if k != "precision"}
+
+
+def rel(got, ref):
+    out = {}
+    for name, a, b in zip(FIELDS, got, ref):
+        if name == "rho-1":
+            a, b = a - 1, b - 1
+        out[name] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    return out
+
+
+@pytest.mark.parametrize("rates", [{}, MRT])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp64_kinetic_les_orszag_tang(L, orc, rates, seed):
+    kw = dict(KW, **rates)
+    fields = inputs.orszag_tang(64, 64, seed=seed)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(kw)), 200)
+    m, st = gpu(L, fields, 200, precision="fp64", **kw)
+    e = rel(m, orc.moments(ref))
+    assert max(e.values()) < 1e-12, e
+    assert np.max(np.abs(st - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("shape", [(37, 23), (5, 3), (1, 9), (9, 1), (1, 1)])
+def test_fp64_kinetic_les_ragged(L, orc, shape):
+    nx, ny = shape
+    fields = inputs.orszag_tang(nx, ny, seed=3, amp=1e-3)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(KW)), 30)
+    _, st = gpu(L, fields, 30, precision="fp64", **KW)
+    assert np.max(np.abs(st - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-4), ("fp32_dev", 3e-5), ("fp16_dev", None)])
+def test_reduced_precision_kinetic_les(L, orc, prec, tol):
+    fields = inputs.orszag_tang(64, 64, seed=0)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(KW)), 200)
+    m, _ = gpu(L, fields, 200, precision=prec, **KW)
+    e = rel(m, orc.moments(ref))
+    if tol is None:
+        assert e["rho-1"] < 5e-2 and max(e[k] for k in FIELDS[1:]) < 2e-2, e
+    else:
+        assert max(e.values()) < tol, e
+
+
+def test_kinetic_les_full_size_sampled(L, orc):
+    n = 1024
+    fields = inputs.turbulence(n, n, seed=1)
+    kw = dict(tau_nu=0.51, tau_eta=0.51, delta=2.0, les=2, s5=1.2, s6=1.2, s7=1.3, s8=1.3)
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.integers(0, n * n, 3000), [0, n - 1, n * n - 1, n * (n - 1)]])
+    for prec, tol in (("fp64", 1e-13), ("fp32", 2e-7)):
+        h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
+        L.lbmhd_init(h, *fields)
+        L.lbmhd_step(h, 70)
+        before = L.lbmhd_get_state(h)
+        L.lbmhd_step(h, 1)
+        after = L.lbmhd_get_state(h)
+        L.lbmhd_destroy(h)
+        ref = orc.step_cells(before, orc.params(C_S=0.0, **kw), idx)
+        assert np.max(np.abs(after.reshape(19, -1)[:, idx].T - ref)) < tol, prec
+
+
+def test_kinetic_les_graph_replay_bitwise(L):
+    fields = inputs.orszag_tang(64, 32, seed=4)
+    outs = []
+    for chunks in ([150], [1] * 5 + [64, 81]):
+        h = L.lbmhd_create(64, 32, L.lbmhd_params_default(precision="fp32", **KW))
+        L.lbmhd_init(h, *fields)
+        for c in chunks:
+            L.lbmhd_step(h, c)
+        outs.append(L.lbmhd_get_state(h))
+        assert L.lbmhd_launch_count(h) == 300  # two kernels per step
+        L.lbmhd_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_kinetic_les_rejected_by_adjoint_and_ensembles(L):
+    import torch
+
+    h = L.lbmhd_create(16, 16, L.lbmhd_params_default(precision="fp64", **KW))
+    f = [torch.tensor(a, device="cuda") for a in inputs.orszag_tang(16, 16)]
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_adjoint_record(h, *f, 4, 2)
+    L.lbmhd_destroy(h)
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd_batch_create([16], [16], [0.6], [0.6], [0.0],
+                             L.lbmhd_params_default(precision="fp32", les=2))
