@@ -192,6 +192,25 @@ def run_reference(args):
     }), flush=True)
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Largest value of x over the ranks of the default process group (x
+    itself without one).  Works over NCCL (CUDA tensor) and gloo (CPU)."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, cells_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS of `world` independent lattices timed together (weak
+    scaling): all ranks' node updates over the slowest rank's time."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def kernel_source_hash() -> str:
     """Hash of the step kernel's sources: DRAM counters taken from another
     version of the kernel are not reported."""
@@ -478,12 +497,8 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_(x):
+        return max_over_ranks(x, dist)
 
     # ---- headline: the chosen precision -----------------------------------
     prec = args.precision
@@ -500,11 +515,11 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         barrier()
-    dt = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    dt = max_over_ranks_(e0.elapsed_time(e1) / 1e3)
     launches = L.lbmhd_launch_count(h) - launches0
     L.lbmhd_sync(h)
     cells = n * n
-    value = world * cells * args.steps / dt / 1e6
+    value = job_rate(world, cells, args.steps, dt)
     bpc = L.lbmhd_bytes_per_cell(prec)
     per_launch_s = (e0.elapsed_time(e1) / 1e3) / args.steps
     achieved = bpc * cells / per_launch_s / 1e9
@@ -521,7 +536,7 @@ def run_ours(args):
         L.lbmhd_init(hk, *fields)
         barrier()
         ksteps = max(2, args.steps // 5)
-        t = max_over_ranks(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
+        t = max_over_ranks_(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
         L.lbmhd_destroy(hk)
         variants["fp32_kinetic_les"] = {
             "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps, "bytes_per_cell": 268,
@@ -535,7 +550,7 @@ def run_ours(args):
             hv = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=vp, **kw))
             L.lbmhd_init(hv, *fields)
             barrier()
-            t = max_over_ranks(timed_steps(L, hv, stream, vsteps, max(3, args.warmup // 10)))
+            t = max_over_ranks_(timed_steps(L, hv, stream, vsteps, max(3, args.warmup // 10)))
             L.lbmhd_destroy(hv)
             vb = L.lbmhd_bytes_per_cell(vp)
             variants[vp] = {
@@ -561,7 +576,7 @@ def run_ours(args):
         L.lbmhd_init(he, *pin_in)
         L.lbmhd_step(he, args.steps)
         L.lbmhd_moments_into(he, *pin_out)
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks_(time.perf_counter() - t0)
         L.lbmhd_destroy(he)
         assert all(np.isfinite(a).all() for a in pin_out)
         e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
@@ -578,7 +593,7 @@ def run_ours(args):
     # ---- batched ensemble vs sequential per-run launches --------------------
     batched = None
     if not args.no_batch:
-        batched = run_batched(L, args, stream, rank, hbm, barrier, max_over_ranks)
+        batched = run_batched(L, args, stream, rank, hbm, barrier, max_over_ranks_)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
