@@ -37,8 +37,13 @@
  * FilterExampleSmall/Large) to Eqs. KinMomentEq and MagMomentEq (Eq.
  * DeltaEqEx is the M_3 case), with periodic central differences of the
  * streamed conserved moments; each step is then two launches (a moments
- * pass and the step) and needs 5 extra planes of device memory.  les = 2 is
- * not available to ensembles or the adjoint.
+ * pass and the step) and needs 5 extra planes of device memory.  les = 3
+ * uses the same moments pass for the cross-helicity closure of Carati et
+ * al. quoted in Sec. 1.1 (Eqs. CHClosureV/B): nu_t = C_S Delta^2
+ * |S^v_ab S^b_ab|^(1/2), eta_t = C_S Delta^2 sgn(j.omega) |j.omega|^(1/2)
+ * from central differences of u and B, tau = tau0 + 3 x (backscatter
+ * allowed, total resistivity kept >= 0).  les = 2 and 3 are not available
+ * to ensembles or the adjoint.
  */
 #ifndef LBMHD_H
 #define LBMHD_H
@@ -85,7 +90,8 @@ typedef struct {
     double s5, s6;         /* energy-flux rates; <= 0: tied to 1/tau_nu */
     double s7, s8;         /* energy rates; <= 0: tied to the local s_nu */
     int32_t les;           /* 0: none; 1: local Smagorinsky rates; 2: the paper's
-                              filtered equilibria (kinetic LES, see below) */
+                              filtered equilibria (kinetic LES); 3: the
+                              cross-helicity closure (see below) */
     int32_t check_finite_every; /* 0: never; k: test rho every k steps */
     double fp16_scale;     /* LBMHD_FP16_DEV: stored = deviation * scale */
     void* stream;          /* cudaStream_t to run on; NULL: library stream */

@@ -47,6 +47,13 @@
  *     in those rules are the resolved conserved moments of the streamed
  *     populations; their gradients are periodic central differences.  The
  *     local Smagorinsky rates of les = 1 are not applied in this mode.
+ *   - les = 3 is the cross-helicity closure of Carati et al. quoted in
+ *     Sec. 1.1 (Eqs. CHClosureV/B): nu_t = C_S Delta^2 |S^v_ab S^b_ab|^(1/2),
+ *     eta_t = C_S Delta^2 sgn(j . omega) |j . omega|^(1/2), from periodic
+ *     central differences of u = (rho u)/rho and B of the streamed
+ *     populations; tau_e = tau_nu + 3 nu_t, tau_m = tau_eta + 3 eta_t
+ *     (nu = (tau - 1/2)/3, Sec. 4.3).  eta_t < 0 (backscatter) is kept, but
+ *     the total resistivity is not allowed below zero: tau_m >= 1/2.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -195,6 +202,7 @@ void orc_geq(double ux, double uy, double bx, double by, double* g) {
  */
 static void collide_impl(const double* z, const double* p, const double* shift, double* out,
                          double* aux);
+static const double* g_taus = NULL; /* les = 3: relaxation times of the node */
 
 void orc_collide_cell(const double* z, const double* p, double* out, double* aux) {
     collide_impl(z, p, NULL, out, aux);
@@ -271,6 +279,10 @@ static void collide_impl(const double* z, const double* p, const double* shift, 
         double Nx2eq = uy * bx - ux * by;
         J = fabs((Ny1 - Ny1eq) - (Nx2 - Nx2eq));
         tau_m = 0.5 * (tau_eta + sqrt(tau_eta * tau_eta + 36.0 * CS * delta * delta * J));
+    }
+    if (g_taus) { /* les = 3: rates from the resolved gradients */
+        tau_e = g_taus[0];
+        tau_m = g_taus[1];
     }
     double s_nu = 1.0 / tau_e;
     double s[NF];
@@ -398,7 +410,7 @@ int orc_step(int nx, int ny, const double* p, double* state, double* work, int n
     (void)nthreads;
     for (int t = 0; t < nsteps; ++t) {
         orc_stream(nx, ny, state, work);
-        if (p[P_LES] == 2.0) {
+        if (p[P_LES] == 2.0 || p[P_LES] == 3.0) {
             kinetic_collide_all(nx, ny, p, work, state);
             continue;
         }
@@ -418,8 +430,36 @@ int orc_step(int nx, int ny, const double* p, double* state, double* work, int n
     return 0;
 }
 
+/* les = 3: relaxation times from the cross-helicity closure, given the
+ * fields (rho, jx, jy, Bx, By) at the node and its four neighbours
+ * (xp, xm, yp, ym). */
+void orc_carati_taus(const double* p, const double* c0, const double* xp, const double* xm,
+                     const double* yp, const double* ym, double* taus) {
+    double cd2 = p[P_CS] * p[P_DELTA] * p[P_DELTA];
+    /* u = j / rho at each point, then central differences */
+    double dux_dx = 0.5 * (xp[1] / xp[0] - xm[1] / xm[0]);
+    double dux_dy = 0.5 * (yp[1] / yp[0] - ym[1] / ym[0]);
+    double duy_dx = 0.5 * (xp[2] / xp[0] - xm[2] / xm[0]);
+    double duy_dy = 0.5 * (yp[2] / yp[0] - ym[2] / ym[0]);
+    double dbx_dx = 0.5 * (xp[3] - xm[3]), dbx_dy = 0.5 * (yp[3] - ym[3]);
+    double dby_dx = 0.5 * (xp[4] - xm[4]), dby_dy = 0.5 * (yp[4] - ym[4]);
+    (void)c0;
+    /* S_ab = (d_b v_a + d_a v_b) / 2 for v = u and v = B */
+    double svxx = dux_dx, svyy = duy_dy, svxy = 0.5 * (dux_dy + duy_dx);
+    double sbxx = dbx_dx, sbyy = dby_dy, sbxy = 0.5 * (dbx_dy + dby_dx);
+    double ss = svxx * sbxx + svyy * sbyy + 2.0 * svxy * sbxy;
+    double nu_t = cd2 * sqrt(fabs(ss));
+    double om = duy_dx - dux_dy, jz = dby_dx - dbx_dy;
+    double jw = jz * om;
+    double eta_t = cd2 * (jw > 0.0 ? 1.0 : (jw < 0.0 ? -1.0 : 0.0)) * sqrt(fabs(jw));
+    taus[0] = p[P_TAU_NU] + 3.0 * nu_t;
+    taus[1] = p[P_TAU_ETA] + 3.0 * eta_t;
+    if (taus[1] < 0.5) taus[1] = 0.5;
+}
+
 /* les = 2: conserved moments of the streamed populations, their periodic
- * central differences, the filtered-equilibrium shifts, then the collision. */
+ * central differences, the filtered-equilibrium shifts, then the collision.
+ * les = 3: the same moments give the cross-helicity closure's rates. */
 static void kinetic_collide_all(int nx, int ny, const double* p, const double* work,
                                 double* state) {
     long N = (long)nx * ny;
@@ -447,9 +487,22 @@ static void kinetic_collide_all(int nx, int ny, const double* p, const double* w
                 grad[2 * q] = 0.5 * (m[q * N + xp] - m[q * N + xm]);
                 grad[2 * q + 1] = 0.5 * (m[q * N + yp] - m[q * N + ym]);
             }
-            orc_kinetic_shift(fld, grad, p[P_DELTA], sh);
             for (int q = 0; q < NPLANE; ++q) z[q] = work[q * N + c];
-            collide_impl(z, p, sh, o, NULL);
+            if (p[P_LES] == 2.0) {
+                orc_kinetic_shift(fld, grad, p[P_DELTA], sh);
+                collide_impl(z, p, sh, o, NULL);
+            } else {
+                double a0[5], axp[5], axm[5], ayp[5], aym[5], taus[2];
+                for (int q = 0; q < 5; ++q) {
+                    a0[q] = m[q * N + c];
+                    axp[q] = m[q * N + xp]; axm[q] = m[q * N + xm];
+                    ayp[q] = m[q * N + yp]; aym[q] = m[q * N + ym];
+                }
+                orc_carati_taus(p, a0, axp, axm, ayp, aym, taus);
+                g_taus = taus;
+                collide_impl(z, p, NULL, o, NULL);
+                g_taus = NULL;
+            }
             for (int q = 0; q < NPLANE; ++q) state[q * N + c] = o[q];
         }
     free(m);
@@ -481,7 +534,18 @@ void orc_step_cells(int nx, int ny, const double* p, const double* state, long n
         double z[NPLANE];
         for (int q = 0; q < NPLANE; ++q)
             z[q] = state[q * N + wrap(y - plane_cy(q), ny) * nx + wrap(x - plane_cx(q), nx)];
-        if (p[P_LES] == 2.0) {
+        if (p[P_LES] == 3.0) {
+            double m0[5], mxp[5], mxm[5], myp[5], mym[5], taus[2];
+            streamed_moments(nx, ny, state, x, y, m0);
+            streamed_moments(nx, ny, state, x + 1, y, mxp);
+            streamed_moments(nx, ny, state, x - 1, y, mxm);
+            streamed_moments(nx, ny, state, x, y + 1, myp);
+            streamed_moments(nx, ny, state, x, y - 1, mym);
+            orc_carati_taus(p, m0, mxp, mxm, myp, mym, taus);
+            g_taus = taus;
+            collide_impl(z, p, NULL, out + c * NPLANE, NULL);
+            g_taus = NULL;
+        } else if (p[P_LES] == 2.0) {
             double m0[5], mxp[5], mxm[5], myp[5], mym[5], grad[10], sh[4];
             streamed_moments(nx, ny, state, x, y, m0);
             streamed_moments(nx, ny, state, x + 1, y, mxp);

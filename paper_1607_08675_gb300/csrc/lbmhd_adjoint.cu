@@ -477,8 +477,8 @@ int lbmhd_adjoint_record(lbmhd_t* h, const double* rho0, const double* ux0, cons
     const int prec = h->p.precision;
     if (prec != LBMHD_FP64 && prec != LBMHD_FP32 && prec != LBMHD_FP32_DEV)
         return afail(LBMHD_EINVAL, "the adjoint supports FP64, FP32 and FP32_DEV storage");
-    if (h->p.les == 2)
-        return afail(LBMHD_EINVAL, "the adjoint supports les 0 and 1 (not the filtered equilibria)");
+    if (h->p.les >= 2)
+        return afail(LBMHD_EINVAL, "the adjoint supports les 0 and 1 (not les 2 or 3)");
     free_tape(h);
     const long long n = (long long)h->geom.nx * h->geom.ny;
     Tape* t = new (std::nothrow) Tape();

@@ -440,8 +440,8 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
         total_cells += (long long)nx[r] * ny[r];
     }
     if (total_cells > (1LL << 31)) return bfail(LBMHD_EINVAL, "ensemble exceeds 2^31 nodes");
-    if (common->les == 2)
-        return bfail(LBMHD_EINVAL, "ensembles support les 0 and 1 (not the filtered equilibria)");
+    if (common->les >= 2)
+        return bfail(LBMHD_EINVAL, "ensembles support les 0 and 1 (not les 2 or 3)");
 
     lbmhd_batch_t* b = new (std::nothrow) lbmhd_batch_t();
     if (!b) return bfail(LBMHD_ENOMEM, "host allocation failed");

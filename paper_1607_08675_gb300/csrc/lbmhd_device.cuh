@@ -99,7 +99,30 @@ struct Coll {
     R inv_s;         // scaled storage: 1 / scale (k18, k36 already divided by scale)
     R scl;           // scaled storage: the scale itself (1 otherwise)
     R d2;            // Delta^2 (filtered equilibria, les = 2)
+    R cd2;           // C_S Delta^2 (cross-helicity closure, les = 3)
 };
+
+// Relaxation times of the cross-helicity closure of Carati et al. (Sec. 1.1,
+// Eqs. CHClosureV/B): nu_t = C_S Delta^2 |S^v_ab S^b_ab|^(1/2) and
+// eta_t = C_S Delta^2 sgn(j omega) |j omega|^(1/2), with S^v, S^b the
+// symmetric gradients of u and B, omega and j the curls; tau = tau0 + 3 x
+// (nu = (tau - 1/2)/3, Sec. 4.3); the total resistivity stays >= 0.
+// gu / gb: d/dx, d/dy of (u_x, u_y) and (B_x, B_y): g[a][0] = d_x v_a.
+template <class R>
+__device__ __forceinline__ void carati_taus(const R (&gu)[2][2], const R (&gb)[2][2], R cd2,
+                                            R tn, R te, R (&taus)[2]) {
+    const R svxy = R(0.5) * (gu[0][1] + gu[1][0]);
+    const R sbxy = R(0.5) * (gb[0][1] + gb[1][0]);
+    const R ss = gu[0][0] * gb[0][0] + gu[1][1] * gb[1][1] + R(2) * svxy * sbxy;
+    const R nu_t = cd2 * sqrt(fabs(ss));
+    const R om = gu[1][0] - gu[0][1], jz = gb[1][0] - gb[0][1];
+    const R jw = jz * om;
+    const R sg = jw > R(0) ? R(1) : (jw < R(0) ? R(-1) : R(0));
+    const R eta_t = cd2 * sg * sqrt(fabs(jw));
+    taus[0] = tn + R(3) * nu_t;
+    const R tm = te + R(3) * eta_t;
+    taus[1] = tm < R(0.5) ? R(0.5) : tm;
+}
 
 // Filtered-equilibrium corrections of the paper's kinetic LES (Sec. 4.1):
 // the filter rules for a product XY, (1/12) dX . dY (Eq. FilterExampleSmall),
@@ -152,7 +175,10 @@ __device__ __forceinline__ void filtered_shift(const R (&fld)[5], const R (&gx)[
 //
 // KIN: relax towards the filtered equilibria, sh = Delta^2 corrections of
 // M_3, M_4, M_7 = M_8 and N_y1 (in the units of d and g).
-template <class R, bool SCALED = false, bool KIN = false>
+//
+// TAUS: use the relaxation times sh[0] (tau_e) and sh[1] (tau_m) given by
+// the caller (cross-helicity closure) instead of the local Smagorinsky ones.
+template <class R, bool SCALED = false, bool KIN = false, bool TAUS = false>
 __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
                                         const R* sh = nullptr) {
     const R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
@@ -206,6 +232,10 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
         const R Nx2 = g[4] - g[8];
         const R J = fabs(Ny1 - Nx2 - R(2) * E);
         tau_m = R(0.5) * (c.te + sqrt_(c.te2 + c.k36 * J));
+    }
+    if (TAUS) {
+        tau_e = sh[0];
+        tau_m = sh[1];
     }
     const R snu = rcp(tau_e);
     const R s7 = c.s7 > R(0) ? c.s7 : snu;

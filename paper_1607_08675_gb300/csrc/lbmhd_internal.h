@@ -20,7 +20,7 @@ struct HostColl {
     int les;
     float scale, inv_scale;  // FP16_DEV encoding
     int tie5, tie6;          // s5 / s6 are the tied 1/tau_nu
-    int kin;                 // les = 2: filtered equilibria (kinetic LES)
+    int kin;                 // 2: filtered equilibria, 3: cross-helicity closure, 0: neither
     double d2;               // Delta^2
 };
 

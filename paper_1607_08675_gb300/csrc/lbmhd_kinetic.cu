@@ -1,12 +1,15 @@
-// lbmhd_kinetic.cu -- the step with the paper's own kinetic LES (les = 2,
-// Sec. 4.1): the collision relaxes towards the filtered equilibria
+// lbmhd_kinetic.cu -- the steps that need gradients of the resolved fields:
+// the paper's own kinetic LES (les = 2, Sec. 4.1) and the cross-helicity
+// closure of Carati et al. (les = 3, Eqs. CHClosureV/B, whose rates are built
+// from u and B gradients).  For les = 2 the collision relaxes towards the filtered equilibria
 // M^eq + Delta^2 M^(Delta), whose corrections need gradients of the
 // resolved conserved moments at the current step.  Two kernels:
 //  1. kin_moments_kernel: rho, jx, jy, Bx, By of the populations streamed
 //     into every node (pull + sums) into five planes;
 //  2. step_kin_kernel: per node, pull the populations, take central
 //     differences of those planes at x +- 1, y +- 1, form the corrections
-//     (filtered_shift) and collide (collide<..., KIN>).
+//     (filtered_shift) and collide (collide<..., KIN>) -- or, for les = 3,
+//     the closure's relaxation times (carati_taus) and collide with them.
 // One node per thread; neighbouring threads share the moment loads in L1.
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(256) kin_moments_kernel(const typename Fmt<P>:
     }
 }
 
-template <int P>
+template <int P, int MODE>
 __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S* __restrict__ src,
                                                        typename Fmt<P>::S* __restrict__ dst,
                                                        const typename Fmt<P>::R* __restrict__ mom,
@@ -77,19 +80,38 @@ __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S*
         const long long xm = (long long)y * nx + wrapk(x - 1, nx);
         const long long yp = (long long)wrapk(y + 1, ny) * nx + x;
         const long long ym = (long long)wrapk(y - 1, ny) * nx + x;
-        R fld[5], gx[5], gy[5], sh[4];
+        if (MODE == 2) {
+            R fld[5], gx[5], gy[5], sh[4];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const R* m = mom + q * ps;
-            fld[q] = m[node];
-            gx[q] = R(0.5) * (m[xp] - m[xm]);
-            gy[q] = R(0.5) * (m[yp] - m[ym]);
+            for (int q = 0; q < 5; ++q) {
+                const R* m = mom + q * ps;
+                fld[q] = m[node];
+                gx[q] = R(0.5) * (m[xp] - m[xm]);
+                gy[q] = R(0.5) * (m[yp] - m[ym]);
+            }
+            filtered_shift<R>(fld, gx, gy, c.d2, sh);
+            if (Fmt<P>::kScaled)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
+            collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
+        } else {
+            // u = j / rho at the four neighbours, B as stored
+            const R* m0 = mom;
+            const R ixp = R(1) / m0[xp], ixm = R(1) / m0[xm], iyp = R(1) / m0[yp],
+                    iym = R(1) / m0[ym];
+            R gu[2][2], gb[2][2], taus[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const R* mj = mom + (1 + a) * ps;
+                const R* mb = mom + (3 + a) * ps;
+                gu[a][0] = R(0.5) * (mj[xp] * ixp - mj[xm] * ixm);
+                gu[a][1] = R(0.5) * (mj[yp] * iyp - mj[ym] * iym);
+                gb[a][0] = R(0.5) * (mb[xp] - mb[xm]);
+                gb[a][1] = R(0.5) * (mb[yp] - mb[ym]);
+            }
+            carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
+            collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
         }
-        filtered_shift<R>(fld, gx, gy, c.d2, sh);
-        if (Fmt<P>::kScaled)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
-        collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
 #pragma unroll
         for (int i = 0; i < 9; ++i) dst[i * ps + node] = Fmt<P>::enc(d[i], i, 1.0f);
 #pragma unroll
@@ -105,6 +127,7 @@ unsigned kin_grid(long long n) {
 template <int P>
 cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const HostColl& hc,
                      cudaStream_t st) {
+    auto step = hc.kin == 3 ? step_kin_kernel<P, 3> : step_kin_kernel<P, 2>;
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
     const long long n = (long long)g.nx * g.ny;
@@ -112,8 +135,8 @@ cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const
                                                        hc.inv_scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    step_kin_kernel<P><<<kin_grid(n), 256, 0, st>>>((const S*)src, (S*)dst, (const R*)mom, g.nx,
-                                                    g.ny, g.ps, coll_for_prec<R>(hc, P));
+    step<<<kin_grid(n), 256, 0, st>>>((const S*)src, (S*)dst, (const R*)mom, g.nx, g.ny, g.ps,
+                                      coll_for_prec<R>(hc, P));
     return cudaGetLastError();
 }
 

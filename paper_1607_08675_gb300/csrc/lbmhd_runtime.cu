@@ -80,7 +80,7 @@ int lbmhd::validate_params(int nx, int ny, const lbmhd_params* p) {
     for (double s : {p->s5, p->s6, p->s7, p->s8})
         if (s > 0.0 && !(s < 2.0)) return fail(LBMHD_EINVAL, "given rates s5..s8 must lie in (0, 2)");
     if (!(p->fp16_scale > 0.0)) return fail(LBMHD_EINVAL, "fp16_scale must be > 0");
-    if (p->les < 0 || p->les > 2) return fail(LBMHD_EINVAL, "les must be 0, 1 or 2");
+    if (p->les < 0 || p->les > 3) return fail(LBMHD_EINVAL, "les must be 0, 1, 2 or 3");
     if (p->check_finite_every < 0) return fail(LBMHD_EINVAL, "check_finite_every must be >= 0");
     // bulk viscosity (Sec. 4.3) at the base rates
     const double s4 = 1.0 / p->tau_nu;
@@ -106,7 +106,7 @@ HostColl make_coll(const lbmhd_params* p) {
     c.s7 = p->s7 > 0.0 ? p->s7 : 0.0;
     c.s8 = p->s8 > 0.0 ? p->s8 : 0.0;
     c.les = p->les == 1 ? 1 : 0;
-    c.kin = p->les == 2 ? 1 : 0;
+    c.kin = p->les >= 2 ? p->les : 0;  // 2: filtered equilibria, 3: cross-helicity
     c.d2 = p->delta * p->delta;
     c.scale = (float)p->fp16_scale;
     c.inv_scale = (float)(1.0 / p->fp16_scale);
@@ -230,7 +230,7 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     }
     h->buf[0] = mem[0];
     h->buf[1] = mem[1];
-    if (p->les == 2) {
+    if (p->les >= 2) {
         const size_t kb = (size_t)5 * h->geom.ps * (p->precision == LBMHD_FP64 ? 8 : 4);
         e = cudaMalloc(&h->d_kin, kb);
         if (e != cudaSuccess) {

@@ -223,6 +223,7 @@ __host__ __device__ inline Coll<R> make_coll_t(double tn, double te, double k18,
     c.inv_s = R(1);
     c.scl = R(1);
     c.d2 = R(0);
+    c.cd2 = (R)(k18 / 18.0);
     return c;
 }
 

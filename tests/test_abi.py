@@ -56,7 +56,7 @@ def test_bytes_per_cell(L):
 @pytest.mark.parametrize("bad,code", [
     (dict(tau_nu=0.5), -1), (dict(tau_eta=0.4), -1), (dict(C_S=-0.1), -1),
     (dict(delta=0.0), -1), (dict(s5=2.5), -1), (dict(precision=9), -1),
-    (dict(tau_nu=float("nan")), -1), (dict(les=3), -1), (dict(fp16_scale=0.0), -1),
+    (dict(tau_nu=float("nan")), -1), (dict(les=4), -1), (dict(fp16_scale=0.0), -1),
     (dict(check_finite_every=-1), -1),
     # xi <= 0 (Sec. 4.3) at tau_nu = 0.6 with s8 large and s7 small
     (dict(s7=0.2, s8=1.9), -1),

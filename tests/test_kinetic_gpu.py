@@ -124,3 +124,49 @@ def test_kinetic_les_rejected_by_adjoint_and_ensembles(L):
     with pytest.raises(L.LBMHDError):
         L.lbmhd_batch_create([16], [16], [0.6], [0.6], [0.0],
                              L.lbmhd_params_default(precision="fp32", les=2))
+
+
+CH = dict(tau_nu=0.6, tau_eta=0.65, C_S=0.3, delta=2.0, les=3)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp64_cross_helicity_closure_orszag_tang(L, orc, seed):
+    fields = inputs.orszag_tang(64, 64, seed=seed)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(CH)), 200)
+    m, st = gpu(L, fields, 200, precision="fp64", **CH)
+    e = rel(m, orc.moments(ref))
+    assert max(e.values()) < 1e-12, e
+    assert np.max(np.abs(st - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-4), ("fp16_dev", None)])
+def test_reduced_precision_cross_helicity(L, orc, prec, tol):
+    fields = inputs.orszag_tang(64, 64, seed=0)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(CH)), 200)
+    m, _ = gpu(L, fields, 200, precision=prec, **CH)
+    e = rel(m, orc.moments(ref))
+    if tol is None:
+        assert e["rho-1"] < 5e-2 and max(e[k] for k in FIELDS[1:]) < 2e-2, e
+    else:
+        assert max(e.values()) < tol, e
+
+
+def test_cross_helicity_ragged_and_sampled(L, orc):
+    for nx, ny in ((37, 23), (5, 3), (1, 9)):
+        fields = inputs.orszag_tang(nx, ny, seed=3, amp=1e-3)
+        ref = orc.step(orc.init(*fields), orc.params(**okw(CH)), 30)
+        _, st = gpu(L, fields, 30, precision="fp64", **CH)
+        assert np.max(np.abs(st - ref)) < 1e-14
+    n = 512
+    fields = inputs.turbulence(n, n, seed=2)
+    kw = dict(CH, tau_nu=0.51, tau_eta=0.51, s5=1.2, s6=1.2, s7=1.3, s8=1.3)
+    h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision="fp64", **kw))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, 40)
+    before = L.lbmhd_get_state(h)
+    L.lbmhd_step(h, 1)
+    after = L.lbmhd_get_state(h)
+    L.lbmhd_destroy(h)
+    idx = np.random.default_rng(3).integers(0, n * n, 2000)
+    ref = orc.step_cells(before, orc.params(**okw(kw)), idx)
+    assert np.max(np.abs(after.reshape(19, -1)[:, idx].T - ref)) < 1e-13

@@ -682,3 +682,67 @@ def test_kinetic_les_emf_is_the_subgrid_induction(orc):
             ratios.append(np.sum(rate * pred) / np.sum(pred * pred))
             assert np.sum(rate * pred) / np.sqrt(np.sum(rate ** 2) * np.sum(pred ** 2)) > 0.99
     assert 0.9 < np.mean(ratios) < 1.08, ratios
+
+
+# ---------------------------------------------------------------- cross-helicity closure (les = 3)
+
+
+def _carati_rates(orc, n, sign, CS, delta, tn, te, amp=0.005, t0=40):
+    """Shear u_x = U sin(ky) with B_x = sign * u_x: measured dE_K/dt and
+    dE_M/dt against the closure's eddy viscosity and resistivity."""
+    x = 2 * np.pi * np.arange(n) / n
+    u = (amp * np.sin(x))[:, None]
+    z = np.zeros_like(u)
+    st = orc.init(1 + z, u, z, sign * u, z)
+    p = orc.params(tau_nu=tn, tau_eta=te, C_S=CS, delta=delta, les=3)
+    s0 = orc.step(st, p, t0 - 1)
+    s1 = orc.step(s0, p, 1)
+    s2 = orc.step(s1, p, 1)
+    ek = lambda s: np.mean(0.5 * orc.moments(s)[0] * orc.moments(s)[1] ** 2)
+    em = lambda s: np.mean(0.5 * orc.moments(s)[3] ** 2)
+    dek, dem = (ek(s2) - ek(s0)) / 2, (em(s2) - em(s0)) / 2
+    m = orc.moments(s1)
+    k = np.fft.fftfreq(n, 1.0 / n) * 2 * np.pi / n
+    du = np.real(np.fft.ifft(1j * k * np.fft.fft(m[1][:, 0])))
+    dbx = np.real(np.fft.ifft(1j * k * np.fft.fft(m[3][:, 0])))
+    cd2 = CS * delta ** 2
+    nu, eta = (tn - 0.5) / 3, (te - 0.5) / 3
+    # S^v:S^b = du dbx / 2; j.omega = (-dbx)(-du) = du dbx
+    nu_t = cd2 * np.sqrt(np.abs(du * dbx) / 2)
+    eta_t = cd2 * np.sign(du * dbx) * np.sqrt(np.abs(du * dbx))
+    pk = -np.mean((nu + nu_t) * du ** 2)
+    pm = -np.mean((eta + eta_t) * dbx ** 2)
+    return dek / pk - 1, dem / pm - 1, -np.mean(nu * du ** 2), -np.mean(eta * dbx ** 2), dek, dem
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_cross_helicity_closure_dissipation(orc, sign):
+    """Eqs. CHClosureV/B: for an Alfvenic shear (B = +u) the eddy viscosity
+    is C_S Delta^2 |S^v:S^b|^(1/2) and the eddy resistivity
+    +C_S Delta^2 |j.omega|^(1/2); for B = -u the resistivity term turns
+    negative (backscatter).  The kinetic and magnetic energies must drain
+    at <(nu + nu_t) |du/dy|^2> and <(eta + eta_t) |dB/dy|^2>."""
+    ek, em, k0, m0, dek, dem = _carati_rates(orc, 64, sign, 1.0, 4.0, 0.6, 0.7)
+    assert abs(ek) < 5e-3 and abs(em) < 5e-3, (ek, em)
+    assert abs(dek / k0 - 1) > 0.05  # the eddy terms are a visible share
+    if sign > 0:
+        assert dem / m0 - 1 > 0.05    # extra resistive drain
+    else:
+        assert dem / m0 - 1 < -0.05   # backscatter: slower drain than eta alone
+
+
+def test_cross_helicity_closure_limits(orc):
+    st = _noneq_state(orc, 12, 10, 2)
+    a = orc.step(st, orc.params(les=3, C_S=0.0), 5)
+    b = orc.step(st, orc.params(les=0), 5)
+    assert np.array_equal(a, b)
+    st = orc.init(*inputs.orszag_tang(24, 20, seed=6))
+    p = orc.params(tau_nu=0.6, tau_eta=0.65, les=3, C_S=0.3, delta=2.0)
+    d0, s1 = orc.diagnostics(st), orc.step(st, p, 100)
+    d1 = orc.diagnostics(s1)
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    for key in ("mom_x", "mom_y", "bsum_x", "bsum_y"):
+        assert abs(d1[key] - d0[key]) < 1e-13 * d0["mass"]
+    idx = np.array([0, 7, 24, 250, 479])
+    full = orc.step(s1, p, 1)
+    assert np.array_equal(orc.step_cells(s1, p, idx), full.reshape(19, -1)[:, idx].T)
