@@ -167,6 +167,17 @@ int lbmhd_get_state(lbmhd_t* h, double* state);
  * Together with lbmhd_get_state this is checkpoint / resume. */
 int lbmhd_set_state(lbmhd_t* h, const double* state);
 
+/* Copy rows [src_row, src_row + nrows) of every population plane of src's
+ * current state into rows [dst_row, ...) of dst's (same nx and precision;
+ * both on this GPU).  Enqueued on dst's stream after src's pending work.
+ * This is the halo exchange of a y-slab domain decomposition (one ghost
+ * row above and below each slab, refreshed after every step): the step
+ * reads only rows y - 1, y, y + 1, so stepping each slab with ghost rows
+ * and exchanging them reproduces the undivided lattice bit for bit.  (The
+ * paper has no counterpart: it is the sharding of the lattice.)
+ * EINVAL for mismatched handles or rows outside a lattice. */
+int lbmhd_copy_rows(lbmhd_t* dst, int dst_row, lbmhd_t* src, int src_row, int nrows);
+
 /* Wait for the handle's stream; reports a pending non-finite density. */
 int lbmhd_sync(lbmhd_t* h);
 

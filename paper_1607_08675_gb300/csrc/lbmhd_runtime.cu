@@ -477,6 +477,36 @@ int lbmhd_set_state(lbmhd_t* h, const double* state) {
     return LBMHD_OK;
 }
 
+int lbmhd_copy_rows(lbmhd_t* dst, int dst_row, lbmhd_t* src, int src_row, int nrows) {
+    int rc = check_handle(dst);
+    if (rc) return rc;
+    rc = check_handle(src);
+    if (rc) return rc;
+    if (dst->geom.nx != src->geom.nx || dst->p.precision != src->p.precision)
+        return fail(LBMHD_EINVAL, "handles differ in nx or precision");
+    if (nrows < 0 || dst_row < 0 || src_row < 0 || dst_row + nrows > dst->geom.ny ||
+        src_row + nrows > src->geom.ny)
+        return fail(LBMHD_EINVAL, "row range outside a lattice");
+    if (!src->initialised) return fail(LBMHD_ESTATE, "source not initialised");
+    if (nrows == 0) return LBMHD_OK;
+    DeviceGuard dg(dst->device);
+    // order after the source's pending work
+    cudaEvent_t ev;
+    LBMHD_CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    LBMHD_CK(dst, cudaEventRecord(ev, src->stream));
+    LBMHD_CK(dst, cudaStreamWaitEvent(dst->stream, ev, 0));
+    cudaEventDestroy(ev);
+    const size_t sb = storage_bytes(dst->p.precision);
+    const size_t row = (size_t)dst->geom.nx * sb;
+    // one strided copy: 19 planes of nrows contiguous rows each
+    LBMHD_CK(dst, cudaMemcpy2DAsync(
+                      (char*)dst->buf[dst->cur] + (size_t)dst_row * row, dst->geom.ps * sb,
+                      (const char*)src->buf[src->cur] + (size_t)src_row * row, src->geom.ps * sb,
+                      (size_t)nrows * row, kNumPlanes, cudaMemcpyDeviceToDevice, dst->stream));
+    dst->initialised = true;
+    return LBMHD_OK;
+}
+
 int lbmhd_sync(lbmhd_t* h) {
     int rc = check_handle(h);
     if (rc) return rc;

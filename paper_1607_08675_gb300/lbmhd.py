@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_get_state": (i, [h, vp]),
                 "lbmhd_set_state": (i, [h, vp]),
                 "lbmhd_sync": (i, [h]),
+                "lbmhd_copy_rows": (i, [h, i, h, i, i]),
                 "lbmhd_step_count": (ctypes.c_int64, [h]),
                 "lbmhd_launch_count": (ctypes.c_int64, [h]),
                 "lbmhd_bytes_per_cell": (i, [i]),
@@ -218,6 +219,10 @@ def lbmhd_get_state(h: Handle) -> np.ndarray:
 def lbmhd_set_state(h: Handle, state):
     st = _host(state, (19,) + h.shape)
     _check(lib().lbmhd_set_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
+
+
+def lbmhd_copy_rows(dst: Handle, dst_row: int, src: Handle, src_row: int, nrows: int):
+    _check(lib().lbmhd_copy_rows(dst.ptr, int(dst_row), src.ptr, int(src_row), int(nrows)))
 
 
 def lbmhd_sync(h: Handle):
