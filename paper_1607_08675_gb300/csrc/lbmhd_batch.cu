@@ -7,7 +7,8 @@
 // units), and unit_run[] maps units to runs.  A persistent grid of
 // co-resident CTAs walks the units of step s, meets at a grid barrier, and
 // goes on with step s + 1 -- `steps_per_launch` steps per launch; the host
-// replays a captured CUDA graph of such launches.  Per thread the work is
+// replays a captured CUDA graph of such launches.  A launch of a single step
+// needs no barrier and covers the units with one CTA each instead.  Per thread the work is
 // step_body, the same code as the single-lattice kernel, so every run
 // evolves bit-identically to its own lbmhd_t.
 //
@@ -285,15 +286,22 @@ cudaError_t launch_batch(lbmhd_batch_t* b, int nsteps, int parity) {
     void* args[] = {&b->d_runs, &b->d_unit_run, &b->nunits, &bufA, &bufB, &nsteps,
                     &parity, &b->d_bar, &b->d_flag, &drop, &scale, &inv_scale};
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)b->grid);
     cfg.blockDim = dim3((unsigned)b->block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident (grid barrier)
     attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    if (nsteps > 1) {
+        cfg.gridDim = dim3((unsigned)b->grid);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    } else {
+        // one step, no barrier: one CTA per work unit, scheduled by the hardware
+        cfg.gridDim = dim3(b->nunits);
+        cfg.attrs = nullptr;
+        cfg.numAttrs = 0;
+    }
     return cudaLaunchKernelExC(&cfg, k, args);
 }
 
