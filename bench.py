@@ -414,7 +414,7 @@ def precision_study(args):
     oracle.build()
     torch.cuda.set_device(0)
     kw = dict(tau_nu=0.51, tau_eta=0.51, C_S=0.1, **TURB_RATES)
-    precs = ("fp64", "fp32", "fp32_dev", "fp16_dev")
+    precs = ("fp64", "ff", "fp32", "fp32_dev", "fp16_dev")
 
     def gpu_run(n, fields, steps, prec):
         h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
@@ -542,8 +542,8 @@ def run_ours(args):
             "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps, "bytes_per_cell": 268,
             "hbm_frac": 268 * cells * ksteps / t / 1e9 / hbm,
             "note": "les=2 (filtered equilibria, Delta=2): moments pass + step per time step"}
-        for vp, vsteps in (("fp64", args.steps // 10), ("fp32_dev", args.steps),
-                           ("fp16_dev", args.steps)):
+        for vp, vsteps in (("fp64", args.steps // 10), ("ff", args.steps // 4),
+                           ("fp32_dev", args.steps), ("fp16_dev", args.steps)):
             if vp == prec:
                 continue
             vsteps = max(2, vsteps)

@@ -74,7 +74,12 @@ typedef enum {
     LBMHD_FP64 = 0,     /* FP64 storage, FP64 arithmetic (parity mode) */
     LBMHD_FP32 = 1,     /* FP32 storage of f and g, FP32 arithmetic */
     LBMHD_FP32_DEV = 2, /* FP32 storage of deviations, FP32 arithmetic */
-    LBMHD_FP16_DEV = 3  /* FP16 storage of scaled deviations, FP32 arithmetic */
+    LBMHD_FP16_DEV = 3, /* FP16 storage of scaled deviations, FP32 arithmetic */
+    LBMHD_FF = 4        /* double-word deviations: each value an FP32 pair
+                           (hi, lo), 8 bytes, 48-bit significand; arithmetic
+                           in double-word on the FP32 units (unit roundoff
+                           2^-48 against FP64's 2^-53).  les 0 and 1 only;
+                           no adjoint; TMA variant not available. */
 } lbmhd_precision;
 
 typedef struct lbmhd_t lbmhd_t;
@@ -164,7 +169,11 @@ int lbmhd_get_state(lbmhd_t* h, double* state);
 
 /* Replace the state with host FP64 planes (layout as lbmhd_get_state),
  * encoded to the storage format; the step counter is left unchanged.
- * Together with lbmhd_get_state this is checkpoint / resume. */
+ * Together with lbmhd_get_state this is checkpoint / resume, bit for bit
+ * for FP64, FP32 and FP16 storage.  LBMHD_FF pairs are rounded to FP64 on
+ * the way out (the stored deviation carries up to 48 bits), so an FF run
+ * resumed from them continues from a state within FP64 rounding of the
+ * original, not bit for bit. */
 int lbmhd_set_state(lbmhd_t* h, const double* state);
 
 /* Copy rows [src_row, src_row + nrows) of every population plane of src's

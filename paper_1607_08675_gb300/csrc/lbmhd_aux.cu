@@ -12,6 +12,7 @@ __device__ __forceinline__ double dev_of(typename Fmt<P>::S v, int p, float inv_
     if constexpr (P == P_FP64) return v - plane_rest<double>(p);
     else if constexpr (P == P_FP32) return (double)v - (double)plane_rest<float>(p);
     else if constexpr (P == P_FP32_DEV) return (double)v;
+    else if constexpr (P == P_FF) return (double)v.x + (double)v.y;
     else return (double)__half2float(__ushort_as_half(v)) * (double)inv_scale;
 }
 // Rest value that dev_of subtracted (FP32 storage subtracts the FP32 weight).
@@ -25,7 +26,10 @@ __device__ __forceinline__ typename Fmt<P>::S enc_d(double absval, double devval
     if constexpr (P == P_FP64) return absval;
     else if constexpr (P == P_FP32) return (float)absval;
     else if constexpr (P == P_FP32_DEV) return (float)devval;
-    else return __half_as_ushort(__float2half_rn((float)(devval * (double)scale)));
+    else if constexpr (P == P_FF) {
+        const float hi = (float)devval;
+        return make_float2(hi, (float)(devval - (double)hi));
+    } else return __half_as_ushort(__float2half_rn((float)(devval * (double)scale)));
 }
 
 // ---- equilibrium initialisation (Sec. 3 equilibria) ----------------------
@@ -293,6 +297,7 @@ static unsigned grid_for(long long n, int block) {
         case P_FP32: { constexpr int P = P_FP32; CALL; } break;         \
         case P_FP32_DEV: { constexpr int P = P_FP32_DEV; CALL; } break; \
         case P_FP16_DEV: { constexpr int P = P_FP16_DEV; CALL; } break; \
+        case P_FF: { constexpr int P = P_FF; CALL; } break;             \
         default: return cudaErrorInvalidValue;                          \
     }
 

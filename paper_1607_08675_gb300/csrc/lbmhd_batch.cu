@@ -221,6 +221,7 @@ const void* pick_kernel(int prec, int vec) {
         LBMHD_K(P_FP32)
         LBMHD_K(P_FP32_DEV)
         LBMHD_K(P_FP16_DEV)
+        LBMHD_K(P_FF)
     }
 #undef LBMHD_K
     return nullptr;
@@ -260,7 +261,9 @@ int upload_runs_t(lbmhd_batch_t* b) {
 
 // (Re)build the unit map and the co-resident grid for the current shape.
 int configure(lbmhd_batch_t* b) {
-    int rc = b->p.precision == LBMHD_FP64 ? upload_runs_t<double>(b) : upload_runs_t<float>(b);
+    int rc = b->p.precision == LBMHD_FP64 ? upload_runs_t<double>(b)
+             : b->p.precision == LBMHD_FF ? upload_runs_t<ff>(b)
+                                          : upload_runs_t<float>(b);
     if (rc) return rc;
     const void* k = pick_kernel(b->p.precision, b->vec);
     if (!k) return bfail(LBMHD_EINVAL, "no batched kernel for this precision / vector width");
@@ -509,7 +512,7 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
     cudaMemset(b->d_flag, 0, sizeof(int));
     // default shape: the widest vector dividing every run's nx, 64 threads
     int v = 4;
-    if (common->precision == LBMHD_FP64) v = 2;
+    if (common->precision == LBMHD_FP64 || common->precision == LBMHD_FF) v = 2;
     for (; v > 1; v >>= 1) {
         bool ok = true;
         for (int r = 0; r < nruns; ++r) ok = ok && nx[r] % v == 0;

@@ -7,6 +7,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "lbmhd_ff.cuh"
+
 namespace lbmhd {
 
 constexpr int kPlanes = 19;  // 9 f_i, then g_k (x, y) for k = 0..4
@@ -31,7 +33,7 @@ __host__ __device__ constexpr R plane_rest(int p) {
 
 // Storage formats.  Every format is decoded to the deviation d = f - w
 // (and g itself) in the arithmetic type R, and encoded back from it.
-enum Prec { P_FP64 = 0, P_FP32 = 1, P_FP32_DEV = 2, P_FP16_DEV = 3 };
+enum Prec { P_FP64 = 0, P_FP32 = 1, P_FP32_DEV = 2, P_FP16_DEV = 3, P_FF = 4 };
 
 template <int P> struct Fmt;
 template <> struct Fmt<P_FP64> {
@@ -69,6 +71,16 @@ template <> struct Fmt<P_FP16_DEV> {
     }
 };
 
+// Double-word deviations: stored (hi, lo), arithmetic in double-word
+// (lbmhd_ff.cuh); the stored pair is the normalised result of the collision.
+template <> struct Fmt<P_FF> {
+    using S = float2;
+    using R = ff;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ R dec(S v, int, float) { return ff(v.x, v.y); }
+    static __device__ __forceinline__ S enc(R d, int, float) { return make_float2(d.hi, d.lo); }
+};
+
 // Reciprocal and square root in the arithmetic type.  FP64 keeps the
 // IEEE-rounded operations (the parity mode); FP32 uses the single-
 // instruction hardware approximations (relative error ~1e-7, far below
@@ -84,6 +96,13 @@ __device__ __forceinline__ float sqrt_(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// x times a small constant k (an integer or a power of two, exact in FP32):
+// R(k) * x; the double-word overload (lbmhd_ff.cuh) scales cheaper.
+template <class R>
+__device__ __forceinline__ R kmul(float k, R x) {
+    return R(k) * x;
 }
 
 // Collision parameters in the arithmetic type.
@@ -181,6 +200,9 @@ __device__ __forceinline__ void filtered_shift(const R (&fld)[5], const R (&gx)[
 template <class R, bool SCALED = false, bool KIN = false, bool TAUS = false>
 __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
                                         const R* sh = nullptr) {
+    // Rational constants, formed at compile time in the arithmetic type.
+    constexpr R k1_3 = R(1) / R(3), k1_6 = R(1) / R(6), k5_3 = R(5) / R(3);
+    constexpr R k1_12 = R(1) / R(12), k1_20 = R(1) / R(20), k1_180 = R(1) / R(180);
     const R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
@@ -193,10 +215,10 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
     const R dsum = (d[5] + d[6]) + (d[7] + d[8]);
     const R m3 = (d[5] - d[6]) + (d[7] - d[8]);
     const R m4 = (d[1] + d[3]) - (d[2] + d[4]);
-    const R m5 = R(2) * (d[3] - d[1]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const R m6 = R(2) * (d[4] - d[2]) + (d[5] + d[6]) - (d[7] + d[8]);
-    const R m7 = R(4) * d[0] - R(5) * ((d[1] + d[2]) + (d[3] + d[4])) + R(4) * dsum;
-    const R m8 = R(4) * d[0] - dsum;
+    const R m5 = kmul(2, d[3] - d[1]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const R m6 = kmul(2, d[4] - d[2]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R m7 = kmul(4, d[0]) - kmul(5, (d[1] + d[2]) + (d[3] + d[4])) + kmul(4, dsum);
+    const R m8 = kmul(4, d[0]) - dsum;
 
     R j2i = (jx * jx + jy * jy) * irho;
     R q3 = jx * jy * irho - bx * by;
@@ -220,18 +242,18 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
     const R n4 = m4 - q4;
     const R n5 = m5 + jx;
     const R n6 = m6 + jy;
-    const R n7 = KIN ? (m7 + R(3) * j2i) - k7 : m7 + R(3) * j2i;
-    const R n8 = KIN ? m8 - ((R(5) / R(3) * dsum9 - R(3) * j2i) + k7)
-                     : m8 - (R(5) / R(3) * dsum9 - R(3) * j2i);
+    const R n7 = KIN ? (m7 + kmul(3, j2i)) - k7 : m7 + kmul(3, j2i);
+    const R n8 = KIN ? m8 - ((k5_3 * dsum9 - kmul(3, j2i)) + k7)
+                     : m8 - (k5_3 * dsum9 - kmul(3, j2i));
 
     R tau_e = c.tn, tau_m = c.te;
     if (c.les) {
-        const R Q = sqrt_(n4 * n4 + R(4) * (n3 * n3));
-        tau_e = R(0.5) * (c.tn + sqrt_(c.tn2 + c.k18 * Q * irho));
+        const R Q = sqrt_(n4 * n4 + kmul(4, n3 * n3));
+        tau_e = kmul(0.5f, c.tn + sqrt_(c.tn2 + c.k18 * Q * irho));
         const R Ny1 = g[3] - g[7];
         const R Nx2 = g[4] - g[8];
-        const R J = fabs(Ny1 - Nx2 - R(2) * E);
-        tau_m = R(0.5) * (c.te + sqrt_(c.te2 + c.k36 * J));
+        const R J = fabs(Ny1 - Nx2 - kmul(2, E));
+        tau_m = kmul(0.5f, c.te + sqrt_(c.te2 + c.k36 * J));
     }
     if (TAUS) {
         tau_e = sh[0];
@@ -241,27 +263,27 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
     const R s7 = c.s7 > R(0) ? c.s7 : snu;
     const R s8 = c.s8 > R(0) ? c.s8 : snu;
 
-    const R a3 = snu * n3 * R(0.25);
-    const R a4 = snu * n4 * R(0.25);
-    const R a5 = c.s5 * n5 * (R(1) / R(12));
-    const R a6 = c.s6 * n6 * (R(1) / R(12));
-    const R a7 = s7 * n7 * (R(1) / R(180));
-    const R a8 = s8 * n8 * (R(1) / R(20));
+    const R a3 = kmul(0.25f, snu * n3);
+    const R a4 = kmul(0.25f, snu * n4);
+    const R a5 = c.s5 * n5 * k1_12;
+    const R a6 = c.s6 * n6 * k1_12;
+    const R a7 = s7 * n7 * k1_180;
+    const R a8 = s8 * n8 * k1_20;
 
-    const R q78 = R(4) * a7 - a8;
-    d[0] -= R(4) * (a7 + a8);
-    d[1] -= a4 - R(2) * a5 - R(5) * a7;
-    d[2] -= -a4 - R(2) * a6 - R(5) * a7;
-    d[3] -= a4 + R(2) * a5 - R(5) * a7;
-    d[4] -= -a4 + R(2) * a6 - R(5) * a7;
+    const R q78 = kmul(4, a7) - a8;
+    d[0] -= kmul(4, a7 + a8);
+    d[1] -= a4 - kmul(2, a5) - kmul(5, a7);
+    d[2] -= -a4 - kmul(2, a6) - kmul(5, a7);
+    d[3] -= a4 + kmul(2, a5) - kmul(5, a7);
+    d[4] -= -a4 + kmul(2, a6) - kmul(5, a7);
     d[5] -= (a3 + a5) + (a6 + q78);
     d[6] -= (a6 - a3) - (a5 - q78);
     d[7] -= (a3 - a5) - (a6 - q78);
     d[8] -= (a5 - a3) - (a6 - q78);
 
     const R sm = rcp(tau_m);
-    const R third = R(1) / R(3), sixth = R(1) / R(6);
-    const R e3 = R(3) * E;
+    const R third = k1_3, sixth = k1_6;
+    const R e3 = kmul(3, E);
     const R geq[10] = {third * bx,        third * by,          // k = 0
                        sixth * bx,        sixth * (by + e3),   // k = 1 (+x)
                        sixth * (bx - e3), sixth * by,          // k = 2 (+y)

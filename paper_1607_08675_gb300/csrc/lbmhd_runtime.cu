@@ -16,7 +16,8 @@ void set_error(const std::string& msg) { g_err = msg; }
 
 size_t storage_bytes(int prec) {
     switch (prec) {
-        case LBMHD_FP64: return 8;
+        case LBMHD_FP64:
+        case LBMHD_FF: return 8;
         case LBMHD_FP32:
         case LBMHD_FP32_DEV: return 4;
         case LBMHD_FP16_DEV: return 2;
@@ -81,6 +82,8 @@ int lbmhd::validate_params(int nx, int ny, const lbmhd_params* p) {
         if (s > 0.0 && !(s < 2.0)) return fail(LBMHD_EINVAL, "given rates s5..s8 must lie in (0, 2)");
     if (!(p->fp16_scale > 0.0)) return fail(LBMHD_EINVAL, "fp16_scale must be > 0");
     if (p->les < 0 || p->les > 3) return fail(LBMHD_EINVAL, "les must be 0, 1, 2 or 3");
+    if (p->precision == LBMHD_FF && p->les >= 2)
+        return fail(LBMHD_EINVAL, "double-word (FF) storage supports les 0 and 1");
     if (p->check_finite_every < 0) return fail(LBMHD_EINVAL, "check_finite_every must be >= 0");
     // bulk viscosity (Sec. 4.3) at the base rates
     const double s4 = 1.0 / p->tau_nu;
@@ -249,16 +252,18 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     // thread in 64-thread blocks for FP32 storage (46.0K MLUPS, 1.03x the
     // measured copy bandwidth), eight nodes (16-byte loads) in 32-thread
     // blocks for FP16 storage (82.0K MLUPS, 0.92x), two nodes in 128-thread
-    // blocks for FP64 (FP64-pipe bound); narrower vectors when nx is not a
-    // multiple.
-    const int want = p->precision == LBMHD_FP64 ? 2 : (p->precision == LBMHD_FP16_DEV ? 8 : 4);
+    // blocks for FP64 (FP64-pipe bound) and for double-word FF storage;
+    // narrower vectors when nx is not a multiple.
+    const int want = p->precision == LBMHD_FP64 || p->precision == LBMHD_FF
+                         ? 2
+                         : (p->precision == LBMHD_FP16_DEV ? 8 : 4);
     h->vec = 1;
     for (int v = want; v > 1; v >>= 1)
         if (nx % v == 0) {
             h->vec = v;
             break;
         }
-    h->block = h->vec == 8 ? 32 : (h->vec == 4 ? 64 : 128);
+    h->block = h->vec == 8 ? 32 : (h->vec == 4 ? 64 : (p->precision == LBMHD_FF ? 256 : 128));
     h->tma_w = 0;
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess ||

@@ -38,7 +38,7 @@ static cudaError_t launch_pv(int block, int max_blocks, const void* src, void* d
 }
 
 bool step_variant_ok(int prec, int vec, int nx) {
-    if (prec < 0 || prec > 3) return false;
+    if (prec < 0 || prec > 4) return false;
     if (vec != 1 && vec != 2 && vec != 4 && !(vec == 8 && prec == P_FP16_DEV)) return false;
     return nx % vec == 0;
 }
@@ -57,6 +57,7 @@ cudaError_t launch_step(int prec, int vec, int block, int max_blocks, const void
         LBMHD_CASE(P_FP64)
         LBMHD_CASE(P_FP32)
         LBMHD_CASE(P_FP32_DEV)
+        LBMHD_CASE(P_FF)
         case P_FP16_DEV:
             switch (vec) {
                 case 1: return launch_pv<P_FP16_DEV, 1>(block, max_blocks, src, dst, g, c, st);

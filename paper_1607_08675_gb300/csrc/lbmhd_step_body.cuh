@@ -30,6 +30,10 @@ template <>
 __device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
     return (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)v, 1);
 }
+template <>
+__device__ __forceinline__ float2 shfl_up1(float2 v) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
 template <class S>
 __device__ __forceinline__ S shfl_down1(S v) {
     return __shfl_down_sync(0xffffffffu, v, 1);
@@ -37,6 +41,11 @@ __device__ __forceinline__ S shfl_down1(S v) {
 template <>
 __device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
     return (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)v, 1);
+}
+template <>
+__device__ __forceinline__ float2 shfl_down1(float2 v) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1),
+                       __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
 // FP16 storage with V = 2W nodes per thread: each plane row segment is W

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbmhd.so")
 
 ABI_VERSION = 1
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_dev": 2, "fp16_dev": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_dev": 2, "fp16_dev": 3, "ff": 4}
 ERRORS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
           -6: "EVERSION", -7: "ESTATE"}
 

@@ -48,8 +48,8 @@ def test_params_default(L):
 
 
 def test_bytes_per_cell(L):
-    assert [L.lbmhd_bytes_per_cell(p) for p in ("fp64", "fp32", "fp32_dev", "fp16_dev")] == [
-        304, 152, 152, 76]
+    assert [L.lbmhd_bytes_per_cell(p) for p in ("fp64", "fp32", "fp32_dev", "fp16_dev", "ff")] == [
+        304, 152, 152, 76, 304]
     assert L.lbmhd_bytes_per_cell(7) == 0
 
 
@@ -58,6 +58,8 @@ def test_bytes_per_cell(L):
     (dict(delta=0.0), -1), (dict(s5=2.5), -1), (dict(precision=9), -1),
     (dict(tau_nu=float("nan")), -1), (dict(les=4), -1), (dict(fp16_scale=0.0), -1),
     (dict(check_finite_every=-1), -1),
+    # double-word storage has no filtered-equilibrium or cross-helicity path
+    (dict(precision=4, les=2), -1), (dict(precision=4, les=3), -1),
     # xi <= 0 (Sec. 4.3) at tau_nu = 0.6 with s8 large and s7 small
     (dict(s7=0.2, s8=1.9), -1),
     (dict(abi_version=2), -6),

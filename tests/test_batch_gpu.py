@@ -59,7 +59,7 @@ def single(L, run, fields, steps, prec):
     return st
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16_dev", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16_dev", "fp64", "ff"])
 def test_batch_runs_equal_single_lattices_bitwise(L, prec):
     steps = 150  # exercises graph replays and a direct tail
     b, fields = make_batch(L, RUNS, prec)

@@ -93,7 +93,7 @@ def test_gloo_two_ranks_match_undivided_oracle(orc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16_dev"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16_dev", "ff"])
 @pytest.mark.parametrize("k", [1, 3, 4])
 def test_slabs_on_one_gpu_match_monolithic(prec, k):
     import torch
