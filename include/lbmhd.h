@@ -247,6 +247,17 @@ int lbmhd_diagnostics_noalloc(const void* state, int precision, int nx, int ny,
 /* Free everything the handle owns.  NULL is accepted. */
 void lbmhd_destroy(lbmhd_t* h);
 
+/* One double-word (LBMHD_FF) operation, elementwise on the device, for
+ * checking that arithmetic against its error bounds.  x, y, out: host
+ * arrays of n doubles (caller-owned).  Each input is first rounded to the
+ * nearest double-word (48-bit significand); out[i] = hi + lo of the
+ * result, computed in FP64.  op: 0 x + y, 1 x - y, 2 x * y, 3 1 / x,
+ * 4 sqrt(x), 5 (float)y * x (the constant-product path; y must hold FP32
+ * values), 6 the normalisation excess |lo| / ulp(hi) of x + y (<= 0.5 for a
+ * normalised pair).  Synchronises.  Errors: EINVAL for NULL pointers, n < 0
+ * or an unknown op; ENOMEM; ECUDA. */
+int lbmhd_ff_eval(int op, const double* x, const double* y, double* out, long long n);
+
 /* ---- adjoint (discrete, hand-written) ------------------------------------
  * Gradients of a scalar function of the final moments with respect to
  * C_S, tau_nu, tau_eta and the initial fields, through the exact transpose

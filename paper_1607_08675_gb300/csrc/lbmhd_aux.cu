@@ -363,3 +363,64 @@ cudaError_t launch_diag(int prec, const void* state, double* partials, double* o
 }
 
 }  // namespace lbmhd
+
+// ---- double-word arithmetic check -----------------------------------------
+namespace lbmhd {
+
+__global__ void ff_eval_kernel(int op, const double* __restrict__ x, const double* __restrict__ y,
+                               double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const ff a(x[i]), b(y[i]);
+        ff r;
+        switch (op) {
+            case 0: r = a + b; break;
+            case 1: r = a - b; break;
+            case 2: r = a * b; break;
+            case 3: r = rcp(a); break;
+            case 4: r = sqrt_(a); break;
+            case 5: r = kmul((float)y[i], a); break;
+            default: {
+                const ff s = a + b;
+                const double ulp = s.hi == 0.0f ? 0.0
+                                   : ldexp(1.0, ilogb((double)s.hi) - 23);
+                out[i] = ulp > 0.0 ? fabs((double)s.lo) / ulp : (s.lo == 0.0f ? 0.0 : 1e30);
+                continue;
+            }
+        }
+        out[i] = (double)r.hi + (double)r.lo;
+    }
+}
+
+}  // namespace lbmhd
+
+extern "C" int lbmhd_ff_eval(int op, const double* x, const double* y, double* out, long long n) {
+    using namespace lbmhd;
+    if (!x || !y || !out || n < 0 || op < 0 || op > 6) {
+        set_error("lbmhd_ff_eval: NULL array, n < 0 or unknown op");
+        return LBMHD_EINVAL;
+    }
+    if (n == 0) return LBMHD_OK;
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, 3 * (size_t)n * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("lbmhd_ff_eval: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LBMHD_ENOMEM : LBMHD_ECUDA;
+    }
+    const size_t b = (size_t)n * sizeof(double);
+    e = cudaMemcpy(d, x, b, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + n, y, b, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        ff_eval_kernel<<<grid_for(n, 256), 256>>>(op, d, d + n, d + 2 * n, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * n, b, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("lbmhd_ff_eval: ") + cudaGetErrorString(e));
+        return LBMHD_ECUDA;
+    }
+    return LBMHD_OK;
+}

@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i)]),
                 "lbmhd_diagnostics_noalloc": (i, [vp, i, i, i, ctypes.c_longlong, d, vp, vp]),
                 "lbmhd_destroy": (None, [h]),
+                "lbmhd_ff_eval": (i, [i, vp, vp, vp, ctypes.c_longlong]),
                 "lbmhd_last_error": (ctypes.c_char_p, []),
                 "lbmhd_adjoint_record": (i, [h, vp, vp, vp, vp, vp, i, i]),
                 "lbmhd_adjoint_backward": (i, [h, vp, vp, vp, vp, vp,
@@ -251,6 +252,24 @@ def lbmhd_get_launch(h: Handle):
     v, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().lbmhd_get_launch(h.ptr, ctypes.byref(v), ctypes.byref(b)))
     return v.value, b.value
+
+
+FF_OPS = {"add": 0, "sub": 1, "mul": 2, "rcp": 3, "sqrt": 4, "kmul": 5, "norm": 6}
+
+
+def lbmhd_ff_eval(op, x, y=None) -> np.ndarray:
+    """One double-word operation elementwise on the device (see
+    include/lbmhd.h); ``op`` a name from FF_OPS or its code."""
+    if isinstance(op, str):
+        op = FF_OPS[op]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x) if y is None else np.ascontiguousarray(y, dtype=np.float64)
+    assert x.shape == y.shape
+    out = np.empty_like(x)
+    _check(lib().lbmhd_ff_eval(int(op), x.ctypes.data_as(ctypes.c_void_p),
+                               y.ctypes.data_as(ctypes.c_void_p),
+                               out.ctypes.data_as(ctypes.c_void_p), x.size))
+    return out
 
 
 def lbmhd_diagnostics_noalloc(state, precision, nx: int, ny: int, plane_stride: int, out,

@@ -145,3 +145,57 @@ def test_ff_diagnostics_match_fp64(L, orc):
     L.lbmhd_destroy(h)
     for k in ("mass", "E_kin", "E_mag", "enstrophy", "cross_helicity", "current_sq"):
         assert abs(d[k] - ref[k]) <= RATIO * 1e-11 * abs(ref[k]), (k, d[k], ref[k])
+
+
+U2 = 2.0 ** -48  # double-word unit roundoff
+
+
+def _ff_round(x):
+    """The nearest double-word (FP32 hi + FP32 lo) to each double, as an
+    exact double: the input the device operation actually sees."""
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def test_ff_primitives_within_their_error_bounds(L):
+    """Each double-word operation against FP64 on 2e5 random operands
+    spanning 11 decades and both signs.  Bounds (u^2 = 2^-48), from the
+    analyses of the methods named in lbmhd_ff.cuh plus the FP64 reference's
+    own rounding: sum 4u^2 (|x| + |y|); product 6u^2 |xy|; reciprocal
+    4u^2; square root 8u^2; product by an FP32 constant 3u^2 (exact for a
+    power of two); every result normalised, |lo| <= ulp(hi) / 2."""
+    rng = np.random.default_rng(11)
+    n = 200_000
+    mag = lambda: 10.0 ** rng.uniform(-8, 3, n) * rng.choice([-1.0, 1.0], n)
+    x, y = mag(), mag()
+    # cancellation and special operands
+    x[:6] = [1.0, 0.5, 3.0, 1e-3, 2.0 / 3.0, 0.1]
+    y[:6] = [-1.0, -0.5, 1.0, -1e-3, -2.0 / 3.0, 0.2]
+    xf, yf = _ff_round(x), _ff_round(y)
+
+    r = L.lbmhd_ff_eval("add", x, y)
+    assert np.all(np.abs(r - (xf + yf)) <= 4 * U2 * (np.abs(xf) + np.abs(yf)))
+    assert np.all(r[[0, 1, 3, 4]] == 0.0)
+    r = L.lbmhd_ff_eval("sub", x, y)
+    assert np.all(np.abs(r - (xf - yf)) <= 4 * U2 * (np.abs(xf) + np.abs(yf)))
+    r = L.lbmhd_ff_eval("mul", x, y)
+    assert np.all(np.abs(r - xf * yf) <= 6 * U2 * np.abs(xf * yf))
+    r = L.lbmhd_ff_eval("rcp", x)
+    assert np.all(np.abs(r * xf - 1.0) <= 4 * U2)
+    ax = np.abs(x)
+    axf = _ff_round(ax)
+    r = L.lbmhd_ff_eval("sqrt", ax)
+    assert np.all(np.abs(r - np.sqrt(axf)) <= 8 * U2 * np.sqrt(axf))
+    squares = np.array([0.0, 1.0, 4.0, 0.25, 16.0, 2.0 ** -40])
+    assert np.array_equal(L.lbmhd_ff_eval("sqrt", squares), np.sqrt(squares))
+    pow2 = np.array([1.0, 2.0, 4.0, 0.25, -0.5, 2.0 ** 20])
+    assert np.array_equal(L.lbmhd_ff_eval("rcp", pow2), 1.0 / pow2)
+    for k in (2.0, 0.25, 0.5, 4.0):
+        r = L.lbmhd_ff_eval("kmul", x, np.full(n, k))
+        assert np.array_equal(r, xf * k), k
+    for k in (3.0, 5.0, 1.0 / 3.0):
+        kf = float(np.float32(k))
+        r = L.lbmhd_ff_eval("kmul", x, np.full(n, kf))
+        assert np.all(np.abs(r - xf * kf) <= 3 * U2 * np.abs(xf * kf)), k
+    assert np.max(L.lbmhd_ff_eval("norm", x, y)) <= 0.5
