@@ -529,19 +529,25 @@ def run_ours(args):
     # ---- other storage forms on the same lattice ---------------------------
     variants = {}
     if not args.no_variants:
-        # the paper's kinetic LES: a moments pass + the step, FP32; algorithmic
-        # bytes per node: 19 reads + 5 writes, 19 + 5 reads + 19 writes
-        hk = L.lbmhd_create(n, n, L.lbmhd_params_default(
-            precision="fp32", **dict(kw, les=2, delta=2.0)))
-        L.lbmhd_init(hk, *fields)
-        barrier()
-        ksteps = max(2, args.steps // 5)
-        t = max_over_ranks_(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
-        L.lbmhd_destroy(hk)
-        variants["fp32_kinetic_les"] = {
-            "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps, "bytes_per_cell": 268,
-            "hbm_frac": 268 * cells * ksteps / t / 1e9 / hbm,
-            "note": "les=2 (filtered equilibria, Delta=2): moments pass + step per time step"}
+        # the paper's kinetic LES, FP32: the fused one-launch kernel (default;
+        # algorithmic bytes per node 19 reads + 19 writes, as a plain step) and
+        # the two-pass kernels (19 reads + 5 writes, 19 + 5 reads + 19 writes)
+        for kname, kvec, kbytes in (("fp32_kinetic_les", 1, 152),
+                                    ("fp32_kinetic_les_two_pass", 0, 268)):
+            hk = L.lbmhd_create(n, n, L.lbmhd_params_default(
+                precision="fp32", **dict(kw, les=2, delta=2.0)))
+            L.lbmhd_set_launch(hk, kvec, 256)
+            L.lbmhd_init(hk, *fields)
+            barrier()
+            ksteps = max(2, args.steps // 5)
+            t = max_over_ranks_(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
+            L.lbmhd_destroy(hk)
+            variants[kname] = {
+                "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps,
+                "bytes_per_cell": kbytes,
+                "hbm_frac": kbytes * cells * ksteps / t / 1e9 / hbm,
+                "note": "les=2 (filtered equilibria, Delta=2), " + (
+                    "fused: one launch per step" if kvec else "moments pass + step")}
         for vp, vsteps in (("fp64", args.steps // 10), ("ff", args.steps // 4),
                            ("fp32_dev", args.steps), ("fp16_dev", args.steps)):
             if vp == prec:

@@ -212,7 +212,12 @@ int64_t lbmhd_launch_count(const lbmhd_t* h);
  * nodes in 32-thread blocks (FP16 storage) or 2 nodes in 128-thread blocks
  * (FP64), falling back to narrower vectors when nx is not a multiple.
  * Results do not depend on the shape (bit for bit).  EINVAL if the shape
- * is not available. */
+ * is not available.
+ * For les 2 and 3 (steps that need moment gradients): vec = 1 selects the
+ * default fused kernel (one launch per step; CTAs of block threads sweep
+ * column strips, `block` ignored on input, reported as strip width + 32),
+ * vec = 0 the two-pass kernels (a moments pass, then the step: two
+ * launches per step).  Both give the same bits. */
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
 

@@ -22,6 +22,11 @@ SOURCES = ["lbmhd_step.cu", "lbmhd_step_tma.cu", "lbmhd_aux.cu", "lbmhd_runtime.
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
+# Per-file flags.  The kinetic-LES kernels are compiled without FMA
+# contraction: the fused and the two-pass kernels perform the same operations
+# in the same order but in differently shaped code, and only with every
+# product rounded on its own is "same operations" also "same bits".
+FILE_FLAGS = {"lbmhd_kinetic.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -54,7 +59,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *extra_flags, "-c",
+               os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -45,11 +45,14 @@ bool step_variant_ok(int prec, int vec, int nx);
 // persistent grid of `grid` CTAs; a timed-out wait sets bit 2 of *status.
 bool tma_variant_ok(int prec, int W, int nx);
 
-// Kinetic-LES step (lbmhd_kinetic.cu): conserved moments of the streamed
+// Kinetic-LES step (lbmhd_kinetic.cu), les = 2 or 3.  Default: one fused
+// launch (column strips swept down in y, moments of the next row in a
+// shared-memory ring).  two_pass: conserved moments of the streamed
 // populations into `mom` (5 planes of the arithmetic type, plane stride
-// g.ps), then the step relaxing towards the filtered equilibria.
-cudaError_t launch_step_kinetic(int prec, const void* src, void* dst, void* mom, const Geom& g,
-                                const HostColl& c, cudaStream_t st);
+// g.ps), then the step.  Both give the same bits.
+cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
+                                void* dst, void* mom, const Geom& g, const HostColl& c,
+                                cudaStream_t st);
 cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
                             const HostColl& c, int* status, cudaStream_t st);
 
@@ -108,6 +111,7 @@ struct lbmhd_t {
     int* d_flag;
     int vec, block;   // register kernel: nodes per thread, threads per block
     int tma_w;        // > 0: TMA-staged kernel with this tile width
+    int kin_two_pass; // les 2, 3: moments pass + step instead of the fused kernel
     int sm_count;
     cudaGraphExec_t graph;
     int graph_steps;

@@ -11,6 +11,10 @@
 //     (filtered_shift) and collide (collide<..., KIN>) -- or, for les = 3,
 //     the closure's relaxation times (carati_taus) and collide with them.
 // One node per thread; neighbouring threads share the moment loads in L1.
+// The default is a fused one-pass kernel (below) with the same arithmetic.
+// This file is compiled without FMA contraction (-fmad=false), so that the
+// two kernels, whose code is shaped differently, round every operation the
+// same way and give the same bits.
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
 
@@ -119,6 +123,177 @@ __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S*
     }
 }
 
+// ---- fused one-pass variant -------------------------------------------------
+// A CTA owns a strip of SW columns [x0, x0 + sw) and a segment of rows
+// [y0, y1), and sweeps down it, keeping the conserved moments of the
+// populations streamed into consecutive rows (the sw strip nodes and the
+// two periodic halo columns x0 - 1, x0 + sw) in a ring of 5 rows in shared
+// memory.  Per row y: phase A forms the moments of row y + 1, a barrier,
+// then phase B collides row y with the central differences from the ring.
+// Phase B takes the pulled populations of its node either from registers,
+// where phase A left them one row earlier (KEEP), or by pulling again (they
+// come from L1/L2).  Every stored value is read from DRAM once, so the step
+// moves the 152 B/node (FP32) of a plain step instead of the two-pass 268 B.
+// Ring of 5 rows: phase A of row y + 2 (slot j + 3) may run while a slower
+// thread still reads rows y - 1 .. y + 1 (slots j .. j + 2) in phase B, and
+// no thread gets further ahead without passing the next barrier.  Moments,
+// differences and collision are the arithmetic of the two-pass kernels, so
+// both give the same bits.
+constexpr int kRing = 5;
+
+template <int P>
+__device__ __forceinline__ void load_pulled(const typename Fmt<P>::S* __restrict__ src, int x,
+                                            int y, int nx, int ny, long long ps,
+                                            typename Fmt<P>::R (&v)[kPlanes]) {
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p)
+        v[p] = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
+                               wrapk(x - plane_cx(p), nx)],
+                           p, 1.0f);
+}
+
+template <int P>
+__device__ __forceinline__ void sum_moments(const typename Fmt<P>::R (&d)[kPlanes], float inv_s,
+                                            typename Fmt<P>::R (&m)[5]) {
+    using R = typename Fmt<P>::R;
+    R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    R bx = (d[9] + d[11]) + (d[13] + d[15]) + d[17];
+    R by = (d[10] + d[12]) + (d[14] + d[16]) + d[18];
+    if (Fmt<P>::kScaled) {
+        drho *= (R)inv_s;
+        jx *= (R)inv_s;
+        jy *= (R)inv_s;
+        bx *= (R)inv_s;
+        by *= (R)inv_s;
+    }
+    m[0] = R(1) + drho;
+    m[1] = jx;
+    m[2] = jy;
+    m[3] = bx;
+    m[4] = by;
+}
+
+template <int P, int MODE, int SW, int MINB, bool KEEP>
+__global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst, int nx,
+    int ny, long long ps, int seglen, Coll<typename Fmt<P>::R> c, float inv_s) {
+    using R = typename Fmt<P>::R;
+    __shared__ R ring[kRing][5][SW + 2];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * SW;
+    const int sw = min(SW, nx - x0);
+    const int y0 = blockIdx.y * seglen;
+    const int y1 = min(y0 + seglen, ny);
+    // moment position of this thread: strip node, left halo, right halo
+    int pos = -1, xm = 0;
+    if (tid < sw) {
+        pos = tid + 1;
+        xm = x0 + tid;
+    } else if (tid == sw) {
+        pos = 0;
+        xm = wrapk(x0 - 1, nx);
+    } else if (tid == sw + 1) {
+        pos = sw + 1;
+        xm = wrapk(x0 + sw, nx);
+    }
+    // phase A: pulled populations of (xm, yy) into v, their moments into a slot
+    auto phase_a = [&](int yy, int slot, R (&v)[kPlanes]) {
+        if (pos < 0) return;
+        load_pulled<P>(src, xm, wrapk(yy, ny), nx, ny, ps, v);
+        R m[5];
+        sum_moments<P>(v, inv_s, m);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) ring[slot][q][pos] = m[q];
+    };
+    // phase B: collide node (x0 + tid, y), pulled populations in v, with the
+    // moment rows y - 1, y, y + 1 in slots sm, s0, sp
+    auto phase_b = [&](int y, int sm, int s0, int sp, const R (&v)[kPlanes]) {
+        const int x = x0 + tid, i = tid + 1;
+        R d[9], g[10];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) d[p] = v[p];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) g[q] = v[9 + q];
+        if (MODE == 2) {
+            R fld[5], gx[5], gy[5], sh[4];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                fld[q] = ring[s0][q][i];
+                gx[q] = R(0.5) * (ring[s0][q][i + 1] - ring[s0][q][i - 1]);
+                gy[q] = R(0.5) * (ring[sp][q][i] - ring[sm][q][i]);
+            }
+            filtered_shift<R>(fld, gx, gy, c.d2, sh);
+            if (Fmt<P>::kScaled)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
+            collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
+        } else {
+            const R ixp = R(1) / ring[s0][0][i + 1], ixm = R(1) / ring[s0][0][i - 1],
+                    iyp = R(1) / ring[sp][0][i], iym = R(1) / ring[sm][0][i];
+            R gu[2][2], gb[2][2], taus[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                gu[a][0] = R(0.5) * (ring[s0][1 + a][i + 1] * ixp - ring[s0][1 + a][i - 1] * ixm);
+                gu[a][1] = R(0.5) * (ring[sp][1 + a][i] * iyp - ring[sm][1 + a][i] * iym);
+                gb[a][0] = R(0.5) * (ring[s0][3 + a][i + 1] - ring[s0][3 + a][i - 1]);
+                gb[a][1] = R(0.5) * (ring[sp][3 + a][i] - ring[sm][3 + a][i]);
+            }
+            carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
+            collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
+        }
+        const long long node = (long long)y * nx + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dst[q * ps + node] = Fmt<P>::enc(d[q], q, 1.0f);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) dst[(9 + q) * ps + node] = Fmt<P>::enc(g[q], 9 + q, 1.0f);
+    };
+    R cur[kPlanes];
+    phase_a(y0 - 1, 0, cur);
+    phase_a(y0, 1, cur);
+    for (int y = y0, j = 0; y < y1; ++y, ++j) {
+        R nxt[kPlanes];
+        phase_a(y + 1, (j + 2) % kRing, nxt);
+        __syncthreads();
+        if (tid < sw) {
+            if (!KEEP) load_pulled<P>(src, x0 + tid, y, nx, ny, ps, cur);
+            phase_b(y, j % kRing, (j + 1) % kRing, (j + 2) % kRing, cur);
+        }
+        if (KEEP)
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) cur[p] = nxt[p];
+    }
+}
+
+// SW: strip width; MINB: CTAs per SM the register budget is sized for;
+// KEEP: phase B takes its populations from registers.  Measured on GB300 at
+// 8192^2 (FP32, les = 2, MLUPS): strip 256 / 3 CTAs / KEEP 35.3K; without
+// KEEP 33.0K; strips of 128 or 96 with more CTAs per SM 29-34K; a variant
+// that issued the next row's loads before phase B (4-row ring) 25-28K
+// (register spills); the two-pass kernels 23.9K.
+template <int P, int SW, int MINB, bool KEEP>
+cudaError_t launch_fused(const void* src, void* dst, const Geom& g, const HostColl& hc,
+                         int sm_count, cudaStream_t st) {
+    using S = typename Fmt<P>::S;
+    using R = typename Fmt<P>::R;
+    const int nstrips = (g.nx + SW - 1) / SW;
+    // about four waves of MINB resident CTAs per SM; each row segment
+    // re-forms two moment rows
+    const long long want = 4LL * MINB * (sm_count > 0 ? sm_count : 1);
+    long long nseg = (want + nstrips - 1) / nstrips;
+    if (nseg > g.ny) nseg = g.ny;
+    if (nseg < 1) nseg = 1;
+    const int seglen = (int)((g.ny + nseg - 1) / nseg);
+    nseg = (g.ny + seglen - 1) / seglen;
+    const dim3 grid((unsigned)nstrips, (unsigned)nseg);
+    auto k = hc.kin == 3 ? step_kin_fused_kernel<P, 3, SW, MINB, KEEP>
+                         : step_kin_fused_kernel<P, 2, SW, MINB, KEEP>;
+    k<<<grid, SW + 32, 0, st>>>((const S*)src, (S*)dst, g.nx, g.ny, g.ps, seglen,
+                                coll_for_prec<R>(hc, P), hc.inv_scale);
+    return cudaGetLastError();
+}
+
 unsigned kin_grid(long long n) {
     long long b = (n + 255) / 256;
     return (unsigned)(b < 1 ? 1 : (b > 65535LL * 8 ? 65535LL * 8 : b));
@@ -142,8 +317,20 @@ cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const
 
 }  // namespace
 
-cudaError_t launch_step_kinetic(int prec, const void* src, void* dst, void* mom, const Geom& g,
-                                const HostColl& c, cudaStream_t st) {
+cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
+                                void* dst, void* mom, const Geom& g, const HostColl& c,
+                                cudaStream_t st) {
+    if (!two_pass) {
+        switch (prec) {
+            case P_FP64: return launch_fused<P_FP64, 128, 2, true>(src, dst, g, c, sm_count, st);
+            case P_FP32: return launch_fused<P_FP32, 256, 3, true>(src, dst, g, c, sm_count, st);
+            case P_FP32_DEV:
+                return launch_fused<P_FP32_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
+            case P_FP16_DEV:
+                return launch_fused<P_FP16_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (prec) {
         case P_FP64: return launch_p<P_FP64>(src, dst, mom, g, c, st);
         case P_FP32: return launch_p<P_FP32>(src, dst, mom, g, c, st);

@@ -146,8 +146,8 @@ int read_flag(lbmhd_t* h) {
 
 cudaError_t launch_one(lbmhd_t* h, const void* src, void* dst) {
     if (h->coll.kin)
-        return launch_step_kinetic(h->p.precision, src, dst, h->d_kin, h->geom, h->coll,
-                                   h->stream);
+        return launch_step_kinetic(h->p.precision, h->kin_two_pass != 0, h->sm_count, src, dst,
+                                   h->d_kin, h->geom, h->coll, h->stream);
     if (h->tma_w > 0)
         return launch_step_tma(h->p.precision, h->tma_w, h->sm_count, src, dst, h->geom, h->coll,
                                h->d_flag, h->stream);
@@ -158,7 +158,7 @@ cudaError_t one_step(lbmhd_t* h) {
     cudaError_t e = launch_one(h, h->buf[h->cur], h->buf[1 - h->cur]);
     if (e == cudaSuccess) {
         h->cur = 1 - h->cur;
-        h->launches += h->coll.kin ? 2 : 1;
+        h->launches += h->coll.kin && h->kin_two_pass ? 2 : 1;
     }
     return e;
 }
@@ -277,7 +277,11 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block) {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (vec == 0) {
+    if (h->coll.kin) {
+        if (vec != 0 && vec != 1)
+            return fail(LBMHD_EINVAL, "les 2, 3: vec 1 (fused kernel) or 0 (two-pass kernels)");
+        h->kin_two_pass = vec == 0;
+    } else if (vec == 0) {
         if (!tma_variant_ok(h->p.precision, block, h->geom.nx))
             return fail(LBMHD_EINVAL,
                         "TMA-staged step: FP32/FP16 storage, tile 128, 256 or 512 dividing nx");
@@ -299,6 +303,11 @@ int lbmhd_set_launch(lbmhd_t* h, int vec, int block) {
 
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block) {
     if (!h || !vec || !block) return fail(LBMHD_EINVAL, "NULL argument");
+    if (h->coll.kin) {
+        *vec = h->kin_two_pass ? 0 : 1;
+        *block = h->kin_two_pass ? 256 : (h->p.precision == LBMHD_FP64 ? 128 : 256) + 32;
+        return LBMHD_OK;
+    }
     *vec = h->tma_w > 0 ? 0 : h->vec;
     *block = h->tma_w > 0 ? h->tma_w : h->block;
     return LBMHD_OK;
@@ -371,7 +380,7 @@ int lbmhd_step(lbmhd_t* h, int n) {
                 h->graph_steps = kGraphSteps;
             }
             LBMHD_CK(h, cudaGraphLaunch(h->graph, h->stream));
-            h->launches += kGraphSteps * (h->coll.kin ? 2 : 1);
+            h->launches += kGraphSteps * (h->coll.kin && h->kin_two_pass ? 2 : 1);
             done += kGraphSteps;
             h->steps += kGraphSteps;
             continue;

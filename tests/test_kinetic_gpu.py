@@ -99,16 +99,20 @@ def test_kinetic_les_full_size_sampled(L, orc):
         assert np.max(np.abs(after.reshape(19, -1)[:, idx].T - ref)) < tol, prec
 
 
-def test_kinetic_les_graph_replay_bitwise(L):
+@pytest.mark.parametrize("vec,per_step", [(1, 1), (0, 2)])
+def test_kinetic_les_graph_replay_bitwise(L, vec, per_step):
+    """Graph replay (runs of 64 steps) equals single launches, for the fused
+    kernel (one launch per step) and the two-pass kernels (two)."""
     fields = inputs.orszag_tang(64, 32, seed=4)
     outs = []
     for chunks in ([150], [1] * 5 + [64, 81]):
         h = L.lbmhd_create(64, 32, L.lbmhd_params_default(precision="fp32", **KW))
+        L.lbmhd_set_launch(h, vec, 256)
         L.lbmhd_init(h, *fields)
         for c in chunks:
             L.lbmhd_step(h, c)
         outs.append(L.lbmhd_get_state(h))
-        assert L.lbmhd_launch_count(h) == 300  # two kernels per step
+        assert L.lbmhd_launch_count(h) == 150 * per_step
         L.lbmhd_destroy(h)
     assert np.array_equal(outs[0], outs[1])
 
@@ -170,3 +174,36 @@ def test_cross_helicity_ragged_and_sampled(L, orc):
     idx = np.random.default_rng(3).integers(0, n * n, 2000)
     ref = orc.step_cells(before, orc.params(**okw(kw)), idx)
     assert np.max(np.abs(after.reshape(19, -1)[:, idx].T - ref)) < 1e-13
+
+
+def _run_variant(L, fields, steps, vec, **kw):
+    ny, nx = fields[0].shape
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(**kw))
+    L.lbmhd_set_launch(h, vec, 256)
+    assert L.lbmhd_get_launch(h)[0] == vec
+    L.lbmhd_init(h, *fields)
+    n0 = L.lbmhd_launch_count(h)
+    L.lbmhd_step(h, steps)
+    launches = L.lbmhd_launch_count(h) - n0
+    st = L.lbmhd_get_state(h)
+    L.lbmhd_destroy(h)
+    return st, launches
+
+
+@pytest.mark.parametrize("les", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev"])
+@pytest.mark.parametrize("shape", [(300, 41), (256, 7), (37, 23), (1, 9), (9, 1), (1, 1),
+                                   (2, 2), (513, 3)])
+def test_fused_kernel_equals_two_pass_bitwise(L, prec, les, shape):
+    """The default one-launch kernel (column strips swept in y, moment rows
+    in a shared-memory ring) gives the two-pass kernels' bits: several
+    strips with a ragged last one, one-row and one-column lattices, strips
+    narrower than the stencil, more row segments than rows."""
+    nx, ny = shape
+    fields = inputs.orszag_tang(nx, ny, seed=6, amp=1e-3)
+    kw = dict(KW, les=les, C_S=0.1 if les == 3 else 0.0, precision=prec)
+    steps = 70
+    a, na = _run_variant(L, fields, steps, 1, **kw)
+    b, nb = _run_variant(L, fields, steps, 0, **kw)
+    assert np.array_equal(a, b)
+    assert (na, nb) == (steps, 2 * steps)
