@@ -268,10 +268,11 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
 
 // SW: strip width; MINB: CTAs per SM the register budget is sized for;
 // KEEP: phase B takes its populations from registers.  Measured on GB300 at
-// 8192^2 (FP32, les = 2, MLUPS): strip 256 / 3 CTAs / KEEP 35.3K; without
-// KEEP 33.0K; strips of 128 or 96 with more CTAs per SM 29-34K; a variant
-// that issued the next row's loads before phase B (4-row ring) 25-28K
-// (register spills); the two-pass kernels 23.9K.
+// 8192^2 (FP32, les = 2, MLUPS, with FMA contraction): strip 256 / 3 CTAs /
+// KEEP 35.3K; without KEEP 33.0K; strips of 128 or 96 with more CTAs per SM
+// 29-34K; a variant that issued the next row's loads before phase B (4-row
+// ring) 25-28K (register spills); the two-pass kernels 23.9K.  Without FMA
+// contraction (as built): 33.5K, two-pass 23.7K.
 template <int P, int SW, int MINB, bool KEEP>
 cudaError_t launch_fused(const void* src, void* dst, const Geom& g, const HostColl& hc,
                          int sm_count, cudaStream_t st) {
