@@ -37,7 +37,8 @@ METRIC = "MLUPS and % of GB300 HBM roofline, plain FP64 vs FP32/batched vs FP64 
 WORKLOAD = ("decaying 2D MHD turbulence 8192x8192, modes 4<=|k|<=8 rms 0.04, C_S=0.1, tau=0.51, "
             "s5=s6=1.2, s7=s8=1.3")
 DTYPES = {"fp64": "f64", "fp32": "f32", "fp32_dev": "f32 (f32 deviation storage)",
-          "fp16_dev": "f32 (f16 deviation storage)"}
+          "fp16_dev": "f32 (f16 deviation storage)",
+          "ff": "double-word f32 pairs (48-bit significand), storage and arithmetic"}
 # Free MRT rates of the turbulence runs (the paper leaves s_5..s_8 open).
 # Tying them to s_nu (the BGK-equivalent choice) is unstable at tau = 0.51
 # in developed MHD turbulence: a 1e-12 perturbation reaches 9% in 300 steps
