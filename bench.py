@@ -6,10 +6,12 @@ Workload (default): decaying 2D MHD turbulence on an 8192 x 8192 periodic
 lattice (random-phase modes 4 <= |k| <= 8, rms 0.04, C_S = 0.1,
 tau = 0.51), FP32 storage and arithmetic, 500 steps timed after warm-up.
 The state (10 GB per buffer) is far larger than L2, so no flush is needed
-between steps.  The same run also times the FP64, FP32-deviation and
-FP16-deviation storage forms on the same lattice (fewer steps), an
-end-to-end pass through the host C ABI (host fields in, host moments
-out), and the CPU oracle on a bounded sample.
+between steps.  The same run also times, on the same lattice, the paper's
+kinetic LES (les = 2; the fused one-launch kernel and the two-pass
+kernels), the FP64, double-word (FF), FP32-deviation and FP16-deviation
+storage forms (fewer steps), an end-to-end pass through the host C ABI
+(host fields in, host moments out), the 256-run ensemble, the adjoint
+(gradients), and the CPU oracle on a bounded sample.
 
 One JSON line is printed by rank 0.  Under torchrun each rank advances its
 own independent lattice (different seed; weak scaling, no data exchange);
