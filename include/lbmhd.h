@@ -78,8 +78,8 @@ typedef enum {
     LBMHD_FF = 4        /* double-word deviations: each value an FP32 pair
                            (hi, lo), 8 bytes, 48-bit significand; arithmetic
                            in double-word on the FP32 units (unit roundoff
-                           2^-48 against FP64's 2^-53).  les 0 and 1 only;
-                           no adjoint; TMA variant not available. */
+                           2^-48 against FP64's 2^-53).  No adjoint; TMA
+                           variant not available. */
 } lbmhd_precision;
 
 typedef struct lbmhd_t lbmhd_t;
@@ -214,10 +214,11 @@ int64_t lbmhd_launch_count(const lbmhd_t* h);
  * Results do not depend on the shape (bit for bit).  EINVAL if the shape
  * is not available.
  * For les 2 and 3 (steps that need moment gradients): vec = 1 selects the
- * default fused kernel (one launch per step; CTAs of block threads sweep
- * column strips, `block` ignored on input, reported as strip width + 32),
- * vec = 0 the two-pass kernels (a moments pass, then the step: two
- * launches per step).  Both give the same bits. */
+ * fused kernel (one launch per step; CTAs sweep column strips; `block`
+ * ignored on input, reported as strip width + 32), vec = 0 the two-pass
+ * kernels (a moments pass, then the step: two launches per step).  Both
+ * give the same bits.  Default: fused for FP32, FP32_DEV, FP16_DEV and for
+ * FF with les 3; two-pass for FP64 and for FF with les 2 (faster there). */
 int lbmhd_set_launch(lbmhd_t* h, int vec, int block);
 int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
 

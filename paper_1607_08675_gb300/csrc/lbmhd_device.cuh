@@ -98,6 +98,20 @@ __device__ __forceinline__ float sqrt_(float x) {
     return r;
 }
 
+// IEEE-rounded reciprocal and square root for float and double (the
+// gradient closures use these); the double-word overloads of lbmhd_ff.cuh
+// are its Newton reciprocal and Dekker square root.
+template <class R>
+__device__ __forceinline__ R recip(R x) {
+    return R(1) / x;
+}
+__device__ __forceinline__ ff recip(ff x) { return rcp(x); }
+template <class R>
+__device__ __forceinline__ R root(R x) {
+    return sqrt(x);
+}
+__device__ __forceinline__ ff root(ff x) { return sqrt_(x); }
+
 // x times a small constant k (an integer or a power of two, exact in FP32):
 // R(k) * x; the double-word overload (lbmhd_ff.cuh) scales cheaper.
 template <class R>
@@ -133,11 +147,11 @@ __device__ __forceinline__ void carati_taus(const R (&gu)[2][2], const R (&gb)[2
     const R svxy = R(0.5) * (gu[0][1] + gu[1][0]);
     const R sbxy = R(0.5) * (gb[0][1] + gb[1][0]);
     const R ss = gu[0][0] * gb[0][0] + gu[1][1] * gb[1][1] + R(2) * svxy * sbxy;
-    const R nu_t = cd2 * sqrt(fabs(ss));
+    const R nu_t = cd2 * root(fabs(ss));
     const R om = gu[1][0] - gu[0][1], jz = gb[1][0] - gb[0][1];
     const R jw = jz * om;
     const R sg = jw > R(0) ? R(1) : (jw < R(0) ? R(-1) : R(0));
-    const R eta_t = cd2 * sg * sqrt(fabs(jw));
+    const R eta_t = cd2 * sg * root(fabs(jw));
     taus[0] = tn + R(3) * nu_t;
     const R tm = te + R(3) * eta_t;
     taus[1] = tm < R(0.5) ? R(0.5) : tm;
@@ -153,16 +167,15 @@ __device__ __forceinline__ void carati_taus(const R (&gu)[2][2], const R (&gb)[2
 template <class R>
 __device__ __forceinline__ void filtered_shift(const R (&fld)[5], const R (&gx)[5],
                                                const R (&gy)[5], R d2, R (&sh)[4]) {
-    const R rho = fld[0], ir = R(1) / fld[0];
+    const R ir = recip(fld[0]);
+    constexpr R twelfth = R(1) / R(12);
     auto dot = [&](int a, int b) { return gx[a] * gx[b] + gy[a] * gy[b]; };
     // ratio rule with Z = rho for fields a, b
     auto ratio = [&](int a, int b) {
         return (dot(a, b) - (fld[a] * dot(0, b) + fld[b] * dot(0, a) - fld[a] * fld[b] * dot(0, 0) * ir) * ir) *
-               (ir * (R(1) / R(12)));
+               (ir * twelfth);
     };
-    const R twelfth = R(1) / R(12);
     const R rxx = ratio(1, 1), ryy = ratio(2, 2), rxy = ratio(1, 2);
-    (void)rho;
     sh[0] = d2 * (rxy - twelfth * dot(3, 4));
     sh[1] = d2 * ((rxx - ryy) - twelfth * (dot(3, 3) - dot(4, 4)));
     sh[2] = d2 * (R(-3) * (rxx + ryy));

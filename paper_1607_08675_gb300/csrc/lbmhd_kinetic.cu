@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S*
         } else {
             // u = j / rho at the four neighbours, B as stored
             const R* m0 = mom;
-            const R ixp = R(1) / m0[xp], ixm = R(1) / m0[xm], iyp = R(1) / m0[yp],
-                    iym = R(1) / m0[ym];
+            const R ixp = recip(m0[xp]), ixm = recip(m0[xm]), iyp = recip(m0[yp]),
+                    iym = recip(m0[ym]);
             R gu[2][2], gb[2][2], taus[2];
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
                 for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
             collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
         } else {
-            const R ixp = R(1) / ring[s0][0][i + 1], ixm = R(1) / ring[s0][0][i - 1],
-                    iyp = R(1) / ring[sp][0][i], iym = R(1) / ring[sm][0][i];
+            const R ixp = recip(ring[s0][0][i + 1]), ixm = recip(ring[s0][0][i - 1]),
+                    iyp = recip(ring[sp][0][i]), iym = recip(ring[sm][0][i]);
             R gu[2][2], gb[2][2], taus[2];
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -329,6 +329,7 @@ cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const voi
                 return launch_fused<P_FP32_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
             case P_FP16_DEV:
                 return launch_fused<P_FP16_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
+            case P_FF: return launch_fused<P_FF, 128, 2, true>(src, dst, g, c, sm_count, st);
         }
         return cudaErrorInvalidValue;
     }
@@ -337,6 +338,7 @@ cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const voi
         case P_FP32: return launch_p<P_FP32>(src, dst, mom, g, c, st);
         case P_FP32_DEV: return launch_p<P_FP32_DEV>(src, dst, mom, g, c, st);
         case P_FP16_DEV: return launch_p<P_FP16_DEV>(src, dst, mom, g, c, st);
+        case P_FF: return launch_p<P_FF>(src, dst, mom, g, c, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -82,8 +82,6 @@ int lbmhd::validate_params(int nx, int ny, const lbmhd_params* p) {
         if (s > 0.0 && !(s < 2.0)) return fail(LBMHD_EINVAL, "given rates s5..s8 must lie in (0, 2)");
     if (!(p->fp16_scale > 0.0)) return fail(LBMHD_EINVAL, "fp16_scale must be > 0");
     if (p->les < 0 || p->les > 3) return fail(LBMHD_EINVAL, "les must be 0, 1, 2 or 3");
-    if (p->precision == LBMHD_FF && p->les >= 2)
-        return fail(LBMHD_EINVAL, "double-word (FF) storage supports les 0 and 1");
     if (p->check_finite_every < 0) return fail(LBMHD_EINVAL, "check_finite_every must be >= 0");
     // bulk viscosity (Sec. 4.3) at the base rates
     const double s4 = 1.0 / p->tau_nu;
@@ -234,7 +232,8 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
     h->buf[0] = mem[0];
     h->buf[1] = mem[1];
     if (p->les >= 2) {
-        const size_t kb = (size_t)5 * h->geom.ps * (p->precision == LBMHD_FP64 ? 8 : 4);
+        const size_t kb = (size_t)5 * h->geom.ps *
+                          (p->precision == LBMHD_FP64 || p->precision == LBMHD_FF ? 8 : 4);
         e = cudaMalloc(&h->d_kin, kb);
         if (e != cudaSuccess) {
             for (int j = 0; j < 5; ++j) cudaFree(mem[j]);
@@ -265,6 +264,12 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
         }
     h->block = h->vec == 8 ? 32 : (h->vec == 4 ? 64 : (p->precision == LBMHD_FF ? 256 : 128));
     h->tma_w = 0;
+    // Kinetic steps: the fused kernel where it is faster (measured at 8192^2
+    // / 4096^2, MLUPS fused vs two-pass: FP32 les 2 33.5K vs 23.7K, les 3
+    // 37.1K vs 22.3K; FP16 38.9K vs 26.6K; FF les 3 8.2K vs 7.2K), the
+    // two-pass kernels where the arithmetic dominates and occupancy wins (FP64
+    // les 2 1.36K vs 1.39K, les 3 1.57K vs 1.58K; FF les 2 6.7K vs 7.6K).
+    h->kin_two_pass = p->precision == LBMHD_FP64 || (p->precision == LBMHD_FF && p->les == 2);
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess ||
         h->sm_count < 1)
@@ -305,7 +310,8 @@ int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block) {
     if (!h || !vec || !block) return fail(LBMHD_EINVAL, "NULL argument");
     if (h->coll.kin) {
         *vec = h->kin_two_pass ? 0 : 1;
-        *block = h->kin_two_pass ? 256 : (h->p.precision == LBMHD_FP64 ? 128 : 256) + 32;
+        const bool wide = h->p.precision == LBMHD_FP64 || h->p.precision == LBMHD_FF;
+        *block = h->kin_two_pass ? 256 : (wide ? 128 : 256) + 32;
         return LBMHD_OK;
     }
     *vec = h->tma_w > 0 ? 0 : h->vec;

@@ -58,8 +58,6 @@ def test_bytes_per_cell(L):
     (dict(delta=0.0), -1), (dict(s5=2.5), -1), (dict(precision=9), -1),
     (dict(tau_nu=float("nan")), -1), (dict(les=4), -1), (dict(fp16_scale=0.0), -1),
     (dict(check_finite_every=-1), -1),
-    # double-word storage has no filtered-equilibrium or cross-helicity path
-    (dict(precision=4, les=2), -1), (dict(precision=4, les=3), -1),
     # xi <= 0 (Sec. 4.3) at tau_nu = 0.6 with s8 large and s7 small
     (dict(s7=0.2, s8=1.9), -1),
     (dict(abi_version=2), -6),

@@ -191,7 +191,7 @@ def _run_variant(L, fields, steps, vec, **kw):
 
 
 @pytest.mark.parametrize("les", [2, 3])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev", "ff"])
 @pytest.mark.parametrize("shape", [(300, 41), (256, 7), (37, 23), (1, 9), (9, 1), (1, 1),
                                    (2, 2), (513, 3)])
 def test_fused_kernel_equals_two_pass_bitwise(L, prec, les, shape):
@@ -207,3 +207,28 @@ def test_fused_kernel_equals_two_pass_bitwise(L, prec, les, shape):
     b, nb = _run_variant(L, fields, steps, 0, **kw)
     assert np.array_equal(a, b)
     assert (na, nb) == (steps, 2 * steps)
+
+
+# Double-word (FF) storage: the FP64 bars scaled by the ratio of the unit
+# roundoffs, 2^-48 / 2^-53 = 32.
+FF_RATIO = 2.0 ** 5
+
+
+@pytest.mark.parametrize("case", ["kin", "kin_mrt", "ch"])
+def test_ff_kinetic_closures_orszag_tang(L, orc, case):
+    kw = {"kin": KW, "kin_mrt": dict(KW, **MRT), "ch": CH}[case]
+    fields = inputs.orszag_tang(64, 64, seed=1)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(kw)), 200)
+    m, st = gpu(L, fields, 200, precision="ff", **kw)
+    e = rel(m, orc.moments(ref))
+    assert max(e.values()) < FF_RATIO * 1e-12, e
+    assert np.max(np.abs(st - ref)) < FF_RATIO * 1e-14
+
+
+@pytest.mark.parametrize("shape", [(37, 23), (5, 3), (1, 9), (9, 1), (1, 1)])
+def test_ff_kinetic_les_ragged(L, orc, shape):
+    nx, ny = shape
+    fields = inputs.orszag_tang(nx, ny, seed=3, amp=1e-3)
+    ref = orc.step(orc.init(*fields), orc.params(**okw(KW)), 30)
+    _, st = gpu(L, fields, 30, precision="ff", **KW)
+    assert np.max(np.abs(st - ref)) < FF_RATIO * 1e-14
