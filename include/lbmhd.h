@@ -133,8 +133,13 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out);
 
 /* Set the state to the local equilibria f^eq(rho, u, B), g^eq(u, B) of
  * Sec. 3 (the paper gives no initial condition; equilibrium is taken).
- * Arguments: five host fields (rho > 0).  Resets the step counter.
- * Synchronises with the handle's stream before returning. */
+ * Arguments: five host fields of nx*ny doubles (x fastest; caller-owned,
+ * not retained).  Pinned host arrays (cudaHostAlloc / cudaHostRegister) are
+ * read by the kernel in place; pageable ones are staged through a
+ * temporary device copy.  rho must be positive and finite: checked on the
+ * device; on failure EINVAL and the handle is uninitialised (step and
+ * moments return ESTATE) until a successful init.  Resets the step
+ * counter.  Synchronises with the handle's stream before returning. */
 int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                const double* bx, const double* by);
 
@@ -151,7 +156,9 @@ int lbmhd_step(lbmhd_t* h, int n);
 
 /* rho, u and B of the current state (conserved by the collision, so they
  * are the moments of Sec. 3 of the last streamed populations).  Host
- * output fields; synchronises. */
+ * output fields of nx*ny doubles (caller-owned); pinned ones are written by
+ * the kernel in place, pageable ones through a temporary device copy.
+ * Synchronises. */
 int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by);
 
 /* As lbmhd_moments, into device fields; enqueued, does not synchronise. */

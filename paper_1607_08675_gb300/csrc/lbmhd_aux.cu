@@ -37,12 +37,13 @@ template <int P>
 __global__ void init_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
                             const double* __restrict__ uy, const double* __restrict__ bx,
                             const double* __restrict__ by, typename Fmt<P>::S* __restrict__ st,
-                            long long n, int nx, long long ps, float scale) {
+                            long long n, int nx, long long ps, float scale, int* bad) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const long long y = c / nx, x = c - y * nx;
         const long long o = y * nx + x;
         const double r = rho[c], u = ux[c], v = uy[c], Bx = bx[c], By = by[c];
+        if (bad && !(r > 0.0 && isfinite(r))) atomicOr(bad, 8);
         const double u2 = u * u + v * v, b2 = Bx * Bx + By * By;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -303,11 +304,11 @@ static unsigned grid_for(long long n, int block) {
 
 cudaError_t launch_init(int prec, const double* rho, const double* ux, const double* uy,
                         const double* bx, const double* by, void* state, const Geom& g,
-                        const HostColl& c, cudaStream_t st) {
+                        const HostColl& c, cudaStream_t st, int* bad) {
     const long long n = (long long)g.nx * g.ny;
     LBMHD_DISPATCH(prec, (init_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(
                              rho, ux, uy, bx, by, (typename Fmt<P>::S*)state, n, g.nx, g.ps,
-                             c.scale)));
+                             c.scale, bad)));
     return cudaGetLastError();
 }
 

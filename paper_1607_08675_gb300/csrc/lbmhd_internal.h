@@ -56,10 +56,12 @@ cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const voi
 cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
                             const HostColl& c, int* status, cudaStream_t st);
 
-// Equilibrium initialisation from five FP64 device fields.
+// Equilibrium initialisation from five FP64 fields the device can address
+// (device memory or pinned host memory).  With bad != nullptr, a density
+// that is not positive and finite sets bit 3 (value 8) of *bad.
 cudaError_t launch_init(int prec, const double* rho, const double* ux, const double* uy,
                         const double* bx, const double* by, void* state, const Geom& g,
-                        const HostColl& c, cudaStream_t st);
+                        const HostColl& c, cudaStream_t st, int* bad = nullptr);
 // Moments of a stored state into five FP64 device fields.
 cudaError_t launch_moments(int prec, const void* state, double* rho, double* ux, double* uy,
                            double* bx, double* by, const Geom& g, const HostColl& c,

@@ -333,26 +333,55 @@ int lbmhd_init_device(lbmhd_t* h, const double* rho, const double* ux, const dou
     return LBMHD_OK;
 }
 
+// The host arrays of lbmhd_init / lbmhd_moments: when all five are pinned
+// host memory the kernels address them in place (over the CPU-GPU link;
+// no staging copy, no temporary); otherwise (pageable memory) they are
+// staged through a temporary device copy.
+static bool device_views(const double* const* host, const double** dev) {
+    for (int i = 0; i < 5; ++i) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess || a.type != cudaMemoryTypeHost ||
+            !a.devicePointer) {
+            cudaGetLastError();
+            return false;
+        }
+        dev[i] = (const double*)a.devicePointer;
+    }
+    return true;
+}
+
 int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                const double* bx, const double* by) {
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho || !ux || !uy || !bx || !by) return fail(LBMHD_EINVAL, "NULL field");
-    const long long n = ncell(h);
-    for (long long c = 0; c < n; ++c)
-        if (!(rho[c] > 0.0) || !is_finite(rho[c]))
-            return fail(LBMHD_EINVAL, "rho must be positive and finite");
     DeviceGuard dg(h->device);
-    double* tmp = nullptr;
-    LBMHD_CK(h, cudaMallocAsync((void**)&tmp, 5 * n * sizeof(double), h->stream));
+    const long long n = ncell(h);
     const double* src[5] = {rho, ux, uy, bx, by};
-    for (int i = 0; i < 5; ++i)
-        LBMHD_CK(h, cudaMemcpyAsync(tmp + i * n, src[i], n * sizeof(double),
-                                    cudaMemcpyHostToDevice, h->stream));
-    rc = lbmhd_init_device(h, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n);
-    cudaFreeAsync(tmp, h->stream);
-    if (rc) return rc;
+    const double* dev[5];
+    double* tmp = nullptr;
+    if (!device_views(src, dev)) {
+        LBMHD_CK(h, cudaMallocAsync((void**)&tmp, 5 * n * sizeof(double), h->stream));
+        for (int i = 0; i < 5; ++i) {
+            LBMHD_CK(h, cudaMemcpyAsync(tmp + i * n, src[i], n * sizeof(double),
+                                        cudaMemcpyHostToDevice, h->stream));
+            dev[i] = tmp + i * n;
+        }
+    }
+    LBMHD_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    LBMHD_CK(h, launch_init(h->p.precision, dev[0], dev[1], dev[2], dev[3], dev[4],
+                            h->buf[h->cur], h->geom, h->coll, h->stream, h->d_flag));
+    if (tmp) LBMHD_CK(h, cudaFreeAsync(tmp, h->stream));
+    int flag = 0;
+    LBMHD_CK(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LBMHD_CK(h, cudaStreamSynchronize(h->stream));
+    h->steps = 0;
+    if (flag & 8) {
+        h->initialised = false;
+        LBMHD_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+        return fail(LBMHD_EINVAL, "rho must be positive and finite (the handle needs a new init)");
+    }
+    h->initialised = true;
     return LBMHD_OK;
 }
 
@@ -420,6 +449,14 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
     if (!h->initialised) return fail(LBMHD_ESTATE, "moments before lbmhd_init");
     DeviceGuard dg(h->device);
     const long long n = ncell(h);
+    double* dst[5] = {rho, ux, uy, bx, by};
+    const double* dev[5];
+    if (device_views(dst, dev)) {
+        rc = lbmhd_moments_device(h, (double*)dev[0], (double*)dev[1], (double*)dev[2],
+                                  (double*)dev[3], (double*)dev[4]);
+        if (rc) return rc;
+        return read_flag(h);
+    }
     double* tmp = nullptr;
     LBMHD_CK(h, cudaMallocAsync((void**)&tmp, 5 * n * sizeof(double), h->stream));
     rc = lbmhd_moments_device(h, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n);
@@ -427,7 +464,6 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
         cudaFreeAsync(tmp, h->stream);
         return rc;
     }
-    double* dst[5] = {rho, ux, uy, bx, by};
     for (int i = 0; i < 5; ++i)
         LBMHD_CK(h, cudaMemcpyAsync(dst[i], tmp + i * n, n * sizeof(double),
                                     cudaMemcpyDeviceToHost, h->stream));

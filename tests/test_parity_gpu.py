@@ -291,3 +291,51 @@ def test_device_entry_points_match_host(L):
     for t, ref in zip(out, m):
         assert np.array_equal(t.cpu().numpy(), ref)
     L.lbmhd_destroy(a)
+
+
+def test_pinned_and_pageable_host_fields_give_the_same_bits(L):
+    """lbmhd_init / lbmhd_moments read and write pinned host arrays in place
+    and stage pageable ones through device copies: same bits either way."""
+    import torch
+
+    nx, ny = 96, 80
+    fields = inputs.turbulence(nx, ny, kmin=2, kmax=5, seed=5)
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in fields]
+    outs = []
+    for src in (fields, pinned):
+        h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision="fp32", **PRESETS["les"]))
+        L.lbmhd_init(h, *src)
+        L.lbmhd_step(h, 20)
+        pg = L.lbmhd_moments(h)
+        pn = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
+        L.lbmhd_moments_into(h, *pn)
+        outs.append((L.lbmhd_get_state(h), pg, pn))
+        L.lbmhd_destroy(h)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][2]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+@pytest.mark.parametrize("pin", [False, True])
+def test_init_rejects_bad_density_on_the_device(L, bad, pin):
+    import torch
+
+    nx, ny = 40, 24
+    fields = [a.copy() for a in inputs.orszag_tang(nx, ny, seed=2)]
+    good = [a.copy() for a in fields]
+    fields[0][7, 13] = bad
+    if pin:
+        fields = [torch.from_numpy(a).pin_memory().numpy() for a in fields]
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision="fp64"))
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd_init(h, *fields)
+    assert e.value.code == -1
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd_step(h, 1)
+    assert e.value.code == -7  # ESTATE: not initialised
+    L.lbmhd_init(h, *good)
+    L.lbmhd_step(h, 3)
+    m = L.lbmhd_moments(h)
+    assert np.isfinite(m[0]).all() and L.lbmhd_step_count(h) == 3
+    L.lbmhd_destroy(h)
