@@ -180,8 +180,21 @@ int lbmhd_get_state(lbmhd_t* h, double* state);
  * for FP64, FP32 and FP16 storage.  LBMHD_FF pairs are rounded to FP64 on
  * the way out (the stored deviation carries up to 48 bits), so an FF run
  * resumed from them continues from a state within FP64 rounding of the
- * original, not bit for bit. */
+ * original, not bit for bit (lbmhd_get_state_raw / lbmhd_set_state_raw are). */
 int lbmhd_set_state(lbmhd_t* h, const double* state);
+
+/* The stored state in the handle's own format, for bit-exact checkpoints of
+ * every format (FF pairs included) at the storage size: a host buffer of
+ * bytes = 19 * nx * ny * value size (8 for FP64 and FF, 4 for FP32 and
+ * FP32_DEV, 2 for FP16_DEV; lbmhd_bytes_per_cell / 2 per node), plane p at
+ * byte offset p * nx * ny * value size, node (x, y) at y * nx + x within a
+ * plane.  Values: FP64 / FP32 populations f and g; FP32_DEV deviations
+ * f - w (g itself); FP16_DEV binary16 deviations times fp16_scale; FF
+ * (hi, lo) FP32 pairs of the deviations.  Caller-owned; synchronises.
+ * EINVAL for NULL or a wrong byte count, ESTATE (get) before init.
+ * set_state_raw leaves the step counter unchanged. */
+int lbmhd_get_state_raw(lbmhd_t* h, void* state, size_t bytes);
+int lbmhd_set_state_raw(lbmhd_t* h, const void* state, size_t bytes);
 
 /* Copy rows [src_row, src_row + nrows) of every population plane of src's
  * current state into rows [dst_row, ...) of dst's (same nx and precision;

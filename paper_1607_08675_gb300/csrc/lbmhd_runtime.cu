@@ -515,6 +515,36 @@ int lbmhd_get_state(lbmhd_t* h, double* state) {
     return LBMHD_OK;
 }
 
+int lbmhd_get_state_raw(lbmhd_t* h, void* state, size_t bytes) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!state) return fail(LBMHD_EINVAL, "state is NULL");
+    const size_t sb = storage_bytes(h->p.precision), n = (size_t)ncell(h);
+    if (bytes != kNumPlanes * n * sb) return fail(LBMHD_EINVAL, "bytes != 19 * nx * ny * value size");
+    if (!h->initialised) return fail(LBMHD_ESTATE, "get_state_raw before lbmhd_init");
+    DeviceGuard dg(h->device);
+    // the 19 planes, packed (the device planes are padded to the plane stride)
+    LBMHD_CK(h, cudaMemcpy2DAsync(state, n * sb, h->buf[h->cur], (size_t)h->geom.ps * sb, n * sb,
+                                  kNumPlanes, cudaMemcpyDeviceToHost, h->stream));
+    LBMHD_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMHD_OK;
+}
+
+int lbmhd_set_state_raw(lbmhd_t* h, const void* state, size_t bytes) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!state) return fail(LBMHD_EINVAL, "state is NULL");
+    const size_t sb = storage_bytes(h->p.precision), n = (size_t)ncell(h);
+    if (bytes != kNumPlanes * n * sb) return fail(LBMHD_EINVAL, "bytes != 19 * nx * ny * value size");
+    DeviceGuard dg(h->device);
+    LBMHD_CK(h, cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->geom.ps * sb, state, n * sb, n * sb,
+                                  kNumPlanes, cudaMemcpyHostToDevice, h->stream));
+    LBMHD_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    LBMHD_CK(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    return LBMHD_OK;
+}
+
 int lbmhd_set_state(lbmhd_t* h, const double* state) {
     int rc = check_handle(h);
     if (rc) return rc;

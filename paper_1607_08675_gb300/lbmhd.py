@@ -75,6 +75,8 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_diagnostics": (i, [h, ctypes.POINTER(Diag)]),
                 "lbmhd_get_state": (i, [h, vp]),
                 "lbmhd_set_state": (i, [h, vp]),
+                "lbmhd_get_state_raw": (i, [h, vp, ctypes.c_size_t]),
+                "lbmhd_set_state_raw": (i, [h, vp, ctypes.c_size_t]),
                 "lbmhd_sync": (i, [h]),
                 "lbmhd_copy_rows": (i, [h, i, h, i, i]),
                 "lbmhd_step_count": (ctypes.c_int64, [h]),
@@ -163,6 +165,10 @@ class Handle:
     def shape(self):
         return (self.ny, self.nx)
 
+    @property
+    def precision(self) -> int:
+        return int(self.params.precision)
+
 
 def lbmhd_create(nx: int, ny: int, params: Params | None = None) -> Handle:
     params = params if params is not None else lbmhd_params_default()
@@ -215,6 +221,28 @@ def lbmhd_get_state(h: Handle) -> np.ndarray:
     st = np.empty((19,) + h.shape)
     _check(lib().lbmhd_get_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
     return st
+
+
+# numpy view of one stored value per format (FF: an FP32 (hi, lo) pair)
+RAW_DTYPES = {0: (np.float64, ()), 1: (np.float32, ()), 2: (np.float32, ()),
+              3: (np.float16, ()), 4: (np.float32, (2,))}
+
+
+def lbmhd_get_state_raw(h: Handle) -> np.ndarray:
+    """The stored state in its own format, shape (19, ny, nx) (FF: (19, ny,
+    nx, 2)); see include/lbmhd.h."""
+    dt, tail = RAW_DTYPES[h.precision]
+    st = np.empty((19,) + h.shape + tail, dtype=dt)
+    _check(lib().lbmhd_get_state_raw(h.ptr, st.ctypes.data_as(ctypes.c_void_p), st.nbytes))
+    return st
+
+
+def lbmhd_set_state_raw(h: Handle, state):
+    dt, tail = RAW_DTYPES[h.precision]
+    st = np.ascontiguousarray(state, dtype=dt)
+    if st.shape != (19,) + h.shape + tail:
+        raise ValueError(f"expected shape {(19,) + h.shape + tail}")
+    _check(lib().lbmhd_set_state_raw(h.ptr, st.ctypes.data_as(ctypes.c_void_p), st.nbytes))
 
 
 def lbmhd_set_state(h: Handle, state):

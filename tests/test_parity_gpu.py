@@ -339,3 +339,43 @@ def test_init_rejects_bad_density_on_the_device(L, bad, pin):
     m = L.lbmhd_moments(h)
     assert np.isfinite(m[0]).all() and L.lbmhd_step_count(h) == 3
     L.lbmhd_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev", "ff"])
+def test_raw_checkpoint_resume_is_bitwise(L, prec):
+    """lbmhd_get_state_raw / lbmhd_set_state_raw keep every format bit for bit
+    (the FP64 view of lbmhd_get_state rounds double-word pairs)."""
+    fields = inputs.orszag_tang(64, 48, seed=7)
+    p = L.lbmhd_params_default(precision=prec, **PRESETS["les_mrt"])
+    a = L.lbmhd_create(64, 48, p)
+    L.lbmhd_init(a, *fields)
+    L.lbmhd_step(a, 150)
+    ref = L.lbmhd_get_state_raw(a)
+    b = L.lbmhd_create(64, 48, p)
+    L.lbmhd_init(b, *fields)
+    L.lbmhd_step(b, 70)
+    ck = L.lbmhd_get_state_raw(b)
+    assert ck.nbytes == 64 * 48 * L.lbmhd_bytes_per_cell(prec) // 2
+    L.lbmhd_destroy(b)
+    c = L.lbmhd_create(64, 48, p)
+    L.lbmhd_set_state_raw(c, ck)
+    L.lbmhd_step(c, 80)
+    got = L.lbmhd_get_state_raw(c)
+    assert got.view(np.uint8).tobytes() == ref.view(np.uint8).tobytes()
+    # the raw values decode to the FP64 view
+    st = L.lbmhd_get_state(c)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4 + [0.0] * 10)[:, None, None]
+    if prec in ("fp64", "fp32"):
+        dec = got.astype(np.float64)
+    elif prec == "fp32_dev":
+        dec = w + got.astype(np.float64)
+    elif prec == "fp16_dev":
+        dec = w + got.astype(np.float64) / 1024.0
+    else:
+        dec = w + (got[..., 0].astype(np.float64) + got[..., 1].astype(np.float64))
+    assert np.max(np.abs(dec - st)) <= 1e-15
+    rc = L.lib().lbmhd_set_state_raw(c.ptr, got.ctypes.data_as(__import__("ctypes").c_void_p),
+                                     got.nbytes - 1)
+    assert rc == -1  # EINVAL: wrong byte count
+    L.lbmhd_destroy(a)
+    L.lbmhd_destroy(c)
