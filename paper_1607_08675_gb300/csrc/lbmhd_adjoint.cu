@@ -231,7 +231,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // One adjoint step.  x: stored state before the forward step (19 planes of
 // storage type S); lin: lambda_{t+1}; lout: lambda_t (type R, same plane
-// stride).  partials: 4 doubles per block.
+// stride).  partials: 4 doubles per block, summed over the steps of a
+// backward sweep -- each block adds into its own slot and the steps run in
+// order on one stream, so the sums are deterministic; one reduction over
+// the blocks follows the sweep.
 template <int P>
 __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
     const typename Fmt<P>::S* __restrict__ x, const typename Fmt<P>::R* __restrict__ lin,
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
     if (threadIdx.x < 4) {
         double s = 0.0;
         for (int w = 0; w < kAdjBlock / 32; ++w) s += red[w][threadIdx.x];
-        partials[(long long)blockIdx.x * 4 + threadIdx.x] = s;
+        partials[(long long)blockIdx.x * 4 + threadIdx.x] += s;  // this block's slot
     }
 }
 
@@ -439,7 +442,7 @@ Coll<R> coll_t(const HostColl& h) {
 
 template <int P>
 cudaError_t run_adj_step(const lbmhd_t* h, const void* x, const void* lin, void* lout,
-                         double* partials, double* acc) {
+                         double* partials) {
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
     const long long n = (long long)h->geom.nx * h->geom.ny;
@@ -449,7 +452,6 @@ cudaError_t run_adj_step(const lbmhd_t* h, const void* x, const void* lin, void*
         coll_t<R>(h->coll), h->coll.inv_scale, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_reduce_kernel<<<1, kAdjBlock, 0, h->stream>>>(partials, (int)grid, acc);
     return cudaGetLastError();
 }
 
@@ -559,6 +561,8 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
     void* lcur = lam;
     void* lnext = lam + plane_bytes_r;
     e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(partials, 0, (size_t)kAdjMaxBlocks * 4 * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(lam, 0, 2 * plane_bytes_r, h->stream);
     if (e == cudaSuccess) {
         switch (prec) {
@@ -581,9 +585,9 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
             // every node of lnext is written by the scatter (a permutation)
             const void* x = seg + (size_t)j * plane_bytes_s;
             switch (prec) {
-                case LBMHD_FP64: e = run_adj_step<P_FP64>(h, x, lcur, lnext, partials, acc); break;
-                case LBMHD_FP32: e = run_adj_step<P_FP32>(h, x, lcur, lnext, partials, acc); break;
-                default: e = run_adj_step<P_FP32_DEV>(h, x, lcur, lnext, partials, acc); break;
+                case LBMHD_FP64: e = run_adj_step<P_FP64>(h, x, lcur, lnext, partials); break;
+                case LBMHD_FP32: e = run_adj_step<P_FP32>(h, x, lcur, lnext, partials); break;
+                default: e = run_adj_step<P_FP32_DEV>(h, x, lcur, lnext, partials); break;
             }
             if (e != cudaSuccess) return fin(acuda(h, e, "adjoint step"));
             void* tmp = lcur;
@@ -603,6 +607,10 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
         e = cudaGetLastError();
         if (e != cudaSuccess) return fin(acuda(h, e, "adjoint init Jacobian"));
     }
+    // the per-block sums over all steps, combined in block order
+    adj_reduce_kernel<<<1, kAdjBlock, 0, h->stream>>>(partials, (int)adj_grid(n), acc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fin(acuda(h, e, "adjoint reduction"));
     double a[4] = {0, 0, 0, 0};
     e = cudaMemcpyAsync(a, acc, sizeof(a), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
