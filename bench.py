@@ -568,6 +568,31 @@ def run_ours(args):
                 "hbm_frac": vb * cells * vsteps / t / 1e9 / hbm,
             }
 
+    # ---- the FP64 diagnostics reduction on the same lattice ----------------
+    # algorithmic bytes: the 19 stored planes, read once (the tiles' halo
+    # rows come from L2)
+    diagnostics = None
+    if not args.no_variants:
+        hd = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **kw))
+        L.lbmhd_init(hd, *fields)
+        L.lbmhd_step(hd, 2)
+        L.lbmhd_diagnostics(hd)
+        barrier()
+        reps = 10
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(reps):
+            L.lbmhd_diagnostics(hd)
+        d1.record(stream)
+        d1.synchronize()
+        t = max_over_ranks_(d0.elapsed_time(d1) / 1e3 / reps)
+        L.lbmhd_destroy(hd)
+        dbytes = L.lbmhd_bytes_per_cell(prec) // 2
+        diagnostics = {"ms": 1e3 * t, "bytes_per_cell": dbytes,
+                       "GBps": dbytes * cells / t / 1e9, "hbm_frac": dbytes * cells / t / 1e9 / hbm,
+                       "note": "lbmhd_diagnostics (12 FP64 sums, div B, |j|^2) of the "
+                               f"{prec} state, per call"}
+
     # ---- end to end through the host C ABI --------------------------------
     e2e = None
     if not args.no_e2e:
@@ -629,6 +654,7 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
                          "bytes_per_cell": bpc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "diagnostics": diagnostics,
             "clocks": clk.summary(), "variants": variants, "batched": batched,
             "adjoint": adjoint,
         }

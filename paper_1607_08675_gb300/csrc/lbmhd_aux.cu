@@ -159,10 +159,19 @@ __global__ void finite_kernel(const typename Fmt<P>::S* __restrict__ st, int* fl
 // Each block walks tiles of 32 x 8 nodes in a fixed order.  A tile's node
 // moments (and a one-node periodic halo) are staged in shared memory, so
 // the central differences of omega, j_z and div B read neighbours from
-// there.  Per-thread FP64 accumulators -> fixed warp-shuffle tree -> fixed
-// cross-warp order -> one partial row per block; a single-block pass then
+// there.  The per-node arithmetic runs in the format's arithmetic type R,
+// as in the step kernels: FP32 for the FP32 and FP16 storage forms, FP64
+// for FP64 storage, double-word for FF.  Each thread sums its nodes in an
+// accumulator type A -- FP64 for FP64 storage, double-word (48-bit
+// significand, on the FP32 pipes) otherwise -- so that no per-node FP64
+// instruction is issued for the FP32 forms (GB300's FP64 pipe is a small
+// fraction of its FP32 pipes; with FP64 per-node arithmetic this pass was
+// FP64-bound at ~10x its memory time).  The per-term FP32 rounding is
+// unbiased, ~1e-7 of a term, and averages down to ~1e-7 / sqrt(N) of a sum.
+// The thread sums then go to FP64: fixed warp-shuffle tree -> fixed
+// cross-warp order -> one partial row per block; a single-block pass
 // combines the rows in block order.  Same lattice, same result, bit for bit.
-constexpr int kTX = 32, kTY = 8, kDiagBlocks = 1024, kNQ = 12;
+constexpr int kOwn = 30, kDiagWarps = 8, kDiagBlocks = 1024, kNQ = 12;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -175,73 +184,184 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-template <int P>
-__global__ void __launch_bounds__(kTX* kTY) diag_kernel(const typename Fmt<P>::S* __restrict__ st,
-                                                         int nx, int ny, long long ps,
-                                                         float inv_scale, double* partials) {
-    __shared__ double sr[kTY + 2][kTX + 2], su[kTY + 2][kTX + 2], sv[kTY + 2][kTX + 2],
-        sbx[kTY + 2][kTX + 2], sby[kTY + 2][kTX + 2];
-    __shared__ double red[kTX * kTY / 32][kNQ];
-    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-    const int tiles_x = (nx + kTX - 1) / kTX, tiles_y = (ny + kTY - 1) / kTY;
-    const int ntiles = tiles_x * tiles_y;
-    double acc[kNQ];
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+// Per-thread accumulator: a += t and its FP64 value.
+template <class R> struct DiagAcc { using A = ff; };
+template <> struct DiagAcc<double> { using A = double; };
+__device__ __forceinline__ void acc_add(double& a, double t) { a += t; }
+__device__ __forceinline__ void acc_add(ff& a, ff t) { a += t; }
+__device__ __forceinline__ void acc_add(ff& a, float t) {  // double-word + FP32
+    const ff s = two_sum(a.hi, t);
+    a = fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_f64(float v) { return v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(ff v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ bool gt(float a, float b) { return a > b; }
+__device__ __forceinline__ bool gt(double a, double b) { return a > b; }
+__device__ __forceinline__ bool gt(ff a, ff b) { return a > b; }
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
-        __syncthreads();
-        for (int h = threadIdx.x; h < (kTX + 2) * (kTY + 2); h += blockDim.x) {
-            const int hx = h % (kTX + 2), hy = h / (kTX + 2);
-            int gx = (x0 + hx - 1) % nx, gy = (y0 + hy - 1) % ny;
-            if (gx < 0) gx += nx;
-            if (gy < 0) gy += ny;
-            double r, u, v, Bx, By;
-            node_moments<P>(st, ps, (long long)gy * nx + gx, inv_scale, r, u, v, Bx, By);
-            sr[hy][hx] = r;
-            su[hy][hx] = u;
-            sv[hy][hx] = v;
-            sbx[hy][hx] = Bx;
-            sby[hy][hx] = By;
-        }
-        __syncthreads();
-        const int x = x0 + tx, y = y0 + ty;
-        if (x < nx && y < ny) {
-            const int hx = tx + 1, hy = ty + 1;
-            const double r = sr[hy][hx], u = su[hy][hx], v = sv[hy][hx];
-            const double Bx = sbx[hy][hx], By = sby[hy][hx];
-            acc[0] += r;
-            acc[1] += r * u;
-            acc[2] += r * v;
-            acc[3] += Bx;
-            acc[4] += By;
-            acc[5] += r * (u * u + v * v);
-            acc[6] += Bx * Bx + By * By;
-            const double om = 0.5 * (sv[hy][hx + 1] - sv[hy][hx - 1]) -
-                              0.5 * (su[hy + 1][hx] - su[hy - 1][hx]);
-            acc[7] += om * om;
-            acc[8] += u * Bx + v * By;
-            const double dv = 0.5 * (sbx[hy][hx + 1] - sbx[hy][hx - 1]) +
-                              0.5 * (sby[hy + 1][hx] - sby[hy - 1][hx]);
-            acc[9] = fmax(acc[9], fabs(dv));
-            acc[10] += dv * dv;
-            const double jz = 0.5 * (sby[hy][hx + 1] - sby[hy][hx - 1]) -
-                              0.5 * (sbx[hy + 1][hx] - sbx[hy - 1][hx]);
-            acc[11] += jz * jz;
+// rho, u, B of the stored node o in the arithmetic type (the sums of the
+// step kernels' collision, deviation form).
+template <int P>
+__device__ __forceinline__ void node_moments_raw(const typename Fmt<P>::S (&raw)[kPlanes],
+                                                 float inv_scale, typename Fmt<P>::R& r,
+                                                 typename Fmt<P>::R& u, typename Fmt<P>::R& v,
+                                                 typename Fmt<P>::R& Bx, typename Fmt<P>::R& By) {
+    using R = typename Fmt<P>::R;
+    R d[9], g[10];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = Fmt<P>::dec(raw[i], i, inv_scale);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) g[q] = Fmt<P>::dec(raw[9 + q], 9 + q, inv_scale);
+    R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    Bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
+    By = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
+    if (Fmt<P>::kScaled) {  // FP16 storage carries the storage scale
+        const R is = (R)inv_scale;
+        dsum9 *= is;
+        jx *= is;
+        jy *= is;
+        Bx *= is;
+        By *= is;
+    }
+    r = R(1) + dsum9;
+    const R ir = rcp(r);
+    u = jx * ir;
+    v = jy * ir;
+}
+
+// Lane shuffles of one value of the arithmetic type.
+__device__ __forceinline__ float shfl_up_r(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn_r(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up_r(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_dn_r(double v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+__device__ __forceinline__ ff shfl_up_r(ff v) { return ff(shfl_up_r(v.hi), shfl_up_r(v.lo)); }
+__device__ __forceinline__ ff shfl_dn_r(ff v) { return ff(shfl_dn_r(v.hi), shfl_dn_r(v.lo)); }
+
+// Work split: a warp sweeps a strip of kOwn columns down a segment of rows.
+// Lane l holds column x0 - 1 + l (periodic): lanes 1..sw own the strip's
+// columns, lanes 0 and sw + 1 the halo columns whose moments the owners'
+// x-differences need; rows y - 1, y, y + 1 stay in registers as the warp
+// moves down, so every node's moments are formed once (plus the halo
+// columns and two rows per segment) from the 19 values stored at it -- no
+// shared memory, no barrier.
+struct DiagPlan {
+    int nstrips, nseg, seglen, nblocks;
+    long long nunits;
+};
+inline DiagPlan diag_plan(const Geom& g) {
+    DiagPlan d;
+    d.nstrips = (g.nx + kOwn - 1) / kOwn;
+    long long nseg = (long long)kDiagBlocks * kDiagWarps / d.nstrips;
+    if (nseg > g.ny) nseg = g.ny;
+    if (nseg < 1) nseg = 1;
+    d.seglen = (int)((g.ny + nseg - 1) / nseg);
+    d.nseg = (int)((g.ny + d.seglen - 1) / d.seglen);
+    d.nunits = (long long)d.nstrips * d.nseg;
+    const long long warps = d.nunits < (long long)kDiagBlocks * kDiagWarps
+                                ? d.nunits
+                                : (long long)kDiagBlocks * kDiagWarps;
+    d.nblocks = (int)((warps + kDiagWarps - 1) / kDiagWarps);
+    return d;
+}
+
+// Two-byte FP16 values are not worth a prefetch register set (measured
+// faster without: 0.94 ms vs 1.15 ms at 8192^2).
+template <int P>
+__global__ void __launch_bounds__(32 * kDiagWarps)
+    diag_kernel(const typename Fmt<P>::S* __restrict__ st, int nx, int ny, long long ps,
+                float inv_scale, int nstrips, int seglen, long long nunits, double* partials) {
+    using R = typename Fmt<P>::R;
+    using A = typename DiagAcc<R>::A;
+    __shared__ double red[kDiagWarps][kNQ];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    A acc[kNQ];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) acc[q] = A(0);
+    R dmax = R(0);
+    const R half = R(0.5);
+    const long long nwarps = (long long)gridDim.x * kDiagWarps;
+    for (long long unit = (long long)blockIdx.x * kDiagWarps + warp; unit < nunits;
+         unit += nwarps) {
+        const int x0 = (int)(unit % nstrips) * kOwn;
+        const int y0 = (int)(unit / nstrips) * seglen;
+        const int y1 = min(y0 + seglen, ny);
+        const int sw = min(kOwn, nx - x0);
+        const bool own = lane >= 1 && lane <= sw;
+        int col = x0 - 1 + (lane <= sw + 1 ? lane : 1);  // idle lanes shadow an owner
+        col = col < 0 ? col + nx : (col >= nx ? col - nx : col);
+        using S = typename Fmt<P>::S;
+        auto load = [&](int y, S (&raw)[kPlanes]) {
+            int yw = y % ny;  // y in [-1, ny + 1]: more than one wrap when ny <= 2
+            if (yw < 0) yw += ny;
+            const long long o = (long long)yw * nx + col;
+#pragma unroll
+            for (int i = 0; i < kPlanes; ++i) raw[i] = st[i * ps + o];
+        };
+        auto moments = [&](const S (&raw)[kPlanes], R (&m)[5]) {
+            node_moments_raw<P>(raw, inv_scale, m[0], m[1], m[2], m[3], m[4]);
+        };
+        // rows y - 1, y, y + 1 (rho, u, v, Bx, By); the stored values of row
+        // y + 2 are in flight while row y is reduced
+        R mp[5], mc[5], mn[5];
+        S ra[kPlanes], rb[kPlanes];
+        load(y0 - 1, ra);
+        load(y0, rb);
+        moments(ra, mp);
+        if (sizeof(S) >= 4) load(y0 + 1, ra);
+        moments(rb, mc);
+        constexpr bool kPrefetch = sizeof(S) >= 4;
+        for (int y = y0; y < y1; ++y) {
+            if (!kPrefetch) load(y + 1, ra);
+            moments(ra, mn);  // row y + 1
+            if (kPrefetch) load(y + 2, ra);
+            // x-neighbours of row y (lanes -1, +1)
+            const R vL = shfl_up_r(mc[2]), vR = shfl_dn_r(mc[2]);
+            const R bxL = shfl_up_r(mc[3]), bxR = shfl_dn_r(mc[3]);
+            const R byL = shfl_up_r(mc[4]), byR = shfl_dn_r(mc[4]);
+            if (own) {
+                const R r = mc[0], u = mc[1], v = mc[2], Bx = mc[3], By = mc[4];
+                acc_add(acc[0], r);
+                acc_add(acc[1], r * u);
+                acc_add(acc[2], r * v);
+                acc_add(acc[3], Bx);
+                acc_add(acc[4], By);
+                acc_add(acc[5], r * (u * u + v * v));
+                acc_add(acc[6], Bx * Bx + By * By);
+                const R om = half * (vR - vL) - half * (mn[1] - mp[1]);
+                acc_add(acc[7], om * om);
+                acc_add(acc[8], u * Bx + v * By);
+                const R dv = half * (bxR - bxL) + half * (mn[4] - mp[4]);
+                const R adv = fabs(dv);
+                if (gt(adv, dmax)) dmax = adv;
+                acc_add(acc[10], dv * dv);
+                const R jz = half * (byR - byL) - half * (mn[3] - mp[3]);
+                acc_add(acc[11], jz * jz);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                mp[q] = mc[q];
+                mc[q] = mn[q];
+            }
         }
     }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) {
-        const double w = q == 9 ? warp_max(acc[q]) : warp_sum(acc[q]);
+        const double t = q == 9 ? to_f64(dmax) : acc_value(acc[q]);
+        const double w = q == 9 ? warp_max(t) : warp_sum(t);
         if (lane == 0) red[warp][q] = w;
     }
     __syncthreads();
     if (threadIdx.x < kNQ) {
         const int q = threadIdx.x;
         double s = red[0][q];
-        for (int w = 1; w < kTX * kTY / 32; ++w) s = q == 9 ? fmax(s, red[w][q]) : s + red[w][q];
+        for (int w = 1; w < kDiagWarps; ++w) s = q == 9 ? fmax(s, red[w][q]) : s + red[w][q];
         partials[(long long)blockIdx.x * kNQ + q] = s;
     }
 }
@@ -346,17 +466,15 @@ cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Ge
     return cudaGetLastError();
 }
 
-int diag_num_blocks(const Geom& g) {
-    const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
-    return (int)(tiles < kDiagBlocks ? tiles : kDiagBlocks);
-}
+int diag_num_blocks(const Geom& g) { return diag_plan(g).nblocks; }
 
 cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
                         const Geom& g, const HostColl& c, cudaStream_t st) {
-    const int nb = diag_num_blocks(g);
-    LBMHD_DISPATCH(prec, (diag_kernel<P><<<nb, kTX * kTY, 0, st>>>(
+    const DiagPlan d = diag_plan(g);
+    const int nb = d.nblocks;
+    LBMHD_DISPATCH(prec, (diag_kernel<P><<<nb, 32 * kDiagWarps, 0, st>>>(
                              (const typename Fmt<P>::S*)state, g.nx, g.ny, g.ps, c.inv_scale,
-                             partials)));
+                             d.nstrips, d.seglen, d.nunits, partials)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, 256, 0, st>>>(partials, nb, (double)g.nx * g.ny, out12);

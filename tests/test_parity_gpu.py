@@ -379,3 +379,28 @@ def test_raw_checkpoint_resume_is_bitwise(L, prec):
     assert rc == -1  # EINVAL: wrong byte count
     L.lbmhd_destroy(a)
     L.lbmhd_destroy(c)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_dev", "fp16_dev"])
+def test_reduced_precision_diagnostics_match_fp64_of_the_same_state(L, orc, prec):
+    """The diagnostics of the FP32 and FP16 forms form each node's terms in
+    FP32 and sum them in double-word: against the oracle's FP64 diagnostics
+    of the same stored state (decoded exactly) the energies, enstrophy,
+    cross helicity and <j^2> agree to 1e-6 relative, the sums of rho, rho u
+    and B and the div B norms to FP32 rounding of the terms."""
+    n = 256
+    fields = inputs.turbulence(n, n, kmin=2, kmax=6, seed=4)
+    h = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=prec, **PRESETS["les_mrt"]))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, 40)
+    got = L.lbmhd_diagnostics(h)
+    ref = orc.diagnostics(L.lbmhd_get_state(h))
+    L.lbmhd_destroy(h)
+    for k in ("mass", "E_kin", "E_mag", "enstrophy", "cross_helicity", "current_sq"):
+        assert abs(got[k] - ref[k]) <= 1e-6 * abs(ref[k]), (k, got[k], ref[k])
+    for k in ("mom_x", "mom_y", "bsum_x", "bsum_y"):
+        assert abs(got[k] - ref[k]) <= 1e-9 * ref["mass"], (k, got[k], ref[k])
+    # central differences of B formed in FP32: ~1e-7 of |B| each
+    brms = np.sqrt(2.0 * ref["E_mag"])
+    for k in ("divB_max", "divB_rms"):
+        assert abs(got[k] - ref[k]) <= 1e-6 * brms, (k, got[k], ref[k])
