@@ -31,6 +31,8 @@
 #include <new>
 #include <string>
 
+#include <type_traits>
+
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
 
@@ -242,10 +244,14 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
     Coll<typename Fmt<P>::R> c, float inv_scale, double* __restrict__ partials) {
     using R = typename Fmt<P>::R;
     const long long n = (long long)nx * ny;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // per-thread sensitivity sums: FP64 for FP64 storage; double-word for
+    // the FP32 forms, which keeps FP64 instructions out of the node loop
+    using Acc = typename std::conditional<sizeof(R) == 8, double, ff>::type;
+    Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
     for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
          node += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(node / nx), xx = (int)(node - (long long)y * nx);
+        // lattices hold at most 2^30 nodes: 32-bit division
+        const int y = (int)((unsigned)node / (unsigned)nx), xx = (int)node - y * nx;
         R d[9], g[10], ld[9], lg[10], md[9], mg[10], th[4];
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) {
@@ -269,13 +275,19 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
             lout[p * ps + dst] = p < 9 ? md[p] : mg[p - 9];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += (double)th[q];
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (sizeof(R) == 8) acc[q] += th[q];
+            else dw_accumulate(acc[q], th[q]);
+        }
     }
     __shared__ double red[kAdjBlock / 32][4];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const double w = warp_sum_d(acc[q]);
+        double a;
+        if constexpr (sizeof(R) == 8) a = acc[q];
+        else a = (double)acc[q].hi + (double)acc[q].lo;
+        const double w = warp_sum_d(a);
         if (lane == 0) red[warp][q] = w;
     }
     __syncthreads();

@@ -189,10 +189,7 @@ template <class R> struct DiagAcc { using A = ff; };
 template <> struct DiagAcc<double> { using A = double; };
 __device__ __forceinline__ void acc_add(double& a, double t) { a += t; }
 __device__ __forceinline__ void acc_add(ff& a, ff t) { a += t; }
-__device__ __forceinline__ void acc_add(ff& a, float t) {  // double-word + FP32
-    const ff s = two_sum(a.hi, t);
-    a = fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
-}
+__device__ __forceinline__ void acc_add(ff& a, float t) { dw_accumulate(a, t); }
 __device__ __forceinline__ double acc_value(double a) { return a; }
 __device__ __forceinline__ double acc_value(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double to_f64(float v) { return v; }

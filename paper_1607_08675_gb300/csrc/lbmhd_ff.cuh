@@ -98,6 +98,13 @@ __device__ __forceinline__ bool operator>(ff a, ff b) {
 }
 __device__ __forceinline__ bool operator<(ff a, ff b) { return b > a; }
 
+// Sums of many FP32 terms without FP64 instructions: a += t in double-word
+// (TwoSum of the high parts, the low parts added, FastTwoSum), 9 operations.
+__device__ __forceinline__ void dw_accumulate(ff& a, float t) {
+    const ff s = two_sum(a.hi, t);
+    a = fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
 __device__ __forceinline__ ff rcp(ff x) {
     const float y = __frcp_rn(x.hi);
     float e = __fmaf_rn(-x.hi, y, 1.0f);  // exact residual of the rounded reciprocal
