@@ -199,13 +199,15 @@ __device__ __forceinline__ bool gt(float a, float b) { return a > b; }
 __device__ __forceinline__ bool gt(double a, double b) { return a > b; }
 __device__ __forceinline__ bool gt(ff a, ff b) { return a > b; }
 
-// rho, u, B of the stored node o in the arithmetic type (the sums of the
-// step kernels' collision, deviation form).
+// Moments of one stored node in the arithmetic type (the sums of the step
+// kernels' collision, deviation form): m = (rho - 1, j_x, j_y, u_x, u_y,
+// B_x, B_y).  rho - 1 and j are sums of the stored values themselves, so
+// the mass and momentum sums carry no rounding of 1 + (rho - 1).
+enum { kDrho = 0, kJx, kJy, kUx, kUy, kBx, kBy, kNM };
 template <int P>
 __device__ __forceinline__ void node_moments_raw(const typename Fmt<P>::S (&raw)[kPlanes],
-                                                 float inv_scale, typename Fmt<P>::R& r,
-                                                 typename Fmt<P>::R& u, typename Fmt<P>::R& v,
-                                                 typename Fmt<P>::R& Bx, typename Fmt<P>::R& By) {
+                                                 float inv_scale,
+                                                 typename Fmt<P>::R (&m)[kNM]) {
     using R = typename Fmt<P>::R;
     R d[9], g[10];
 #pragma unroll
@@ -215,8 +217,8 @@ __device__ __forceinline__ void node_moments_raw(const typename Fmt<P>::S (&raw)
     R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    Bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
-    By = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
+    R Bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
+    R By = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
     if (Fmt<P>::kScaled) {  // FP16 storage carries the storage scale
         const R is = (R)inv_scale;
         dsum9 *= is;
@@ -225,10 +227,14 @@ __device__ __forceinline__ void node_moments_raw(const typename Fmt<P>::S (&raw)
         Bx *= is;
         By *= is;
     }
-    r = R(1) + dsum9;
-    const R ir = rcp(r);
-    u = jx * ir;
-    v = jy * ir;
+    const R ir = rcp(R(1) + dsum9);
+    m[kDrho] = dsum9;
+    m[kJx] = jx;
+    m[kJy] = jy;
+    m[kUx] = jx * ir;
+    m[kUy] = jy * ir;
+    m[kBx] = Bx;
+    m[kBy] = By;
 }
 
 // Lane shuffles of one value of the arithmetic type.
@@ -301,12 +307,12 @@ __global__ void __launch_bounds__(32 * kDiagWarps)
 #pragma unroll
             for (int i = 0; i < kPlanes; ++i) raw[i] = st[i * ps + o];
         };
-        auto moments = [&](const S (&raw)[kPlanes], R (&m)[5]) {
-            node_moments_raw<P>(raw, inv_scale, m[0], m[1], m[2], m[3], m[4]);
+        auto moments = [&](const S (&raw)[kPlanes], R (&m)[kNM]) {
+            node_moments_raw<P>(raw, inv_scale, m);
         };
-        // rows y - 1, y, y + 1 (rho, u, v, Bx, By); the stored values of row
-        // y + 2 are in flight while row y is reduced
-        R mp[5], mc[5], mn[5];
+        // moments of rows y - 1, y, y + 1; the stored values of row y + 2 are
+        // in flight while row y is reduced
+        R mp[kNM], mc[kNM], mn[kNM];
         S ra[kPlanes], rb[kPlanes];
         load(y0 - 1, ra);
         load(y0, rb);
@@ -319,30 +325,30 @@ __global__ void __launch_bounds__(32 * kDiagWarps)
             moments(ra, mn);  // row y + 1
             if (kPrefetch) load(y + 2, ra);
             // x-neighbours of row y (lanes -1, +1)
-            const R vL = shfl_up_r(mc[2]), vR = shfl_dn_r(mc[2]);
-            const R bxL = shfl_up_r(mc[3]), bxR = shfl_dn_r(mc[3]);
-            const R byL = shfl_up_r(mc[4]), byR = shfl_dn_r(mc[4]);
+            const R vL = shfl_up_r(mc[kUy]), vR = shfl_dn_r(mc[kUy]);
+            const R bxL = shfl_up_r(mc[kBx]), bxR = shfl_dn_r(mc[kBx]);
+            const R byL = shfl_up_r(mc[kBy]), byR = shfl_dn_r(mc[kBy]);
             if (own) {
-                const R r = mc[0], u = mc[1], v = mc[2], Bx = mc[3], By = mc[4];
-                acc_add(acc[0], r);
-                acc_add(acc[1], r * u);
-                acc_add(acc[2], r * v);
+                const R u = mc[kUx], v = mc[kUy], Bx = mc[kBx], By = mc[kBy];
+                acc_add(acc[0], mc[kDrho]);  // the node count is added at the end
+                acc_add(acc[1], mc[kJx]);
+                acc_add(acc[2], mc[kJy]);
                 acc_add(acc[3], Bx);
                 acc_add(acc[4], By);
-                acc_add(acc[5], r * (u * u + v * v));
+                acc_add(acc[5], mc[kJx] * u + mc[kJy] * v);  // rho |u|^2
                 acc_add(acc[6], Bx * Bx + By * By);
-                const R om = half * (vR - vL) - half * (mn[1] - mp[1]);
+                const R om = half * (vR - vL) - half * (mn[kUx] - mp[kUx]);
                 acc_add(acc[7], om * om);
                 acc_add(acc[8], u * Bx + v * By);
-                const R dv = half * (bxR - bxL) + half * (mn[4] - mp[4]);
+                const R dv = half * (bxR - bxL) + half * (mn[kBy] - mp[kBy]);
                 const R adv = fabs(dv);
                 if (gt(adv, dmax)) dmax = adv;
                 acc_add(acc[10], dv * dv);
-                const R jz = half * (byR - byL) - half * (mn[3] - mp[3]);
+                const R jz = half * (byR - byL) - half * (mn[kBx] - mp[kBx]);
                 acc_add(acc[11], jz * jz);
             }
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
+            for (int q = 0; q < kNM; ++q) {
                 mp[q] = mc[q];
                 mc[q] = mn[q];
             }
@@ -387,7 +393,7 @@ __global__ void diag_final_kernel(const double* __restrict__ partials, int nbloc
             for (int w = 1; w < 256 / 32; ++w) s[q] = q == 9 ? fmax(s[q], red[w][q]) : s[q] + red[w][q];
         }
         const double inv = 1.0 / ncell;
-        out[0] = s[0];
+        out[0] = ncell + s[0];  // the threads summed rho - 1
         out[1] = s[1];
         out[2] = s[2];
         out[3] = s[3];
