@@ -221,7 +221,10 @@ __device__ __forceinline__ void collide_adjoint(const R (&d)[9], const R (&g)[10
 namespace {
 
 constexpr int kAdjBlock = 256;
-constexpr int kAdjMaxBlocks = 4096;
+// Grid of at most 8 blocks per SM of a 152-SM GB300 (two resident at 114
+// registers, four waves): each thread sweeps many nodes, so its one final
+// conversion and warp reduction of the sensitivity sums stays small.
+constexpr int kAdjMaxBlocks = 8 * 152;
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
