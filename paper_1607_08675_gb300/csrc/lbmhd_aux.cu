@@ -261,15 +261,17 @@ struct DiagPlan {
 inline DiagPlan diag_plan(const Geom& g) {
     DiagPlan d;
     d.nstrips = (g.nx + kOwn - 1) / kOwn;
-    long long nseg = (long long)kDiagBlocks * kDiagWarps / d.nstrips;
+    // about three full waves on GB300 (152 SMs, two blocks of 256 threads
+    // resident each): 912 blocks, within the kDiagBlocks scratch rows
+    constexpr long long kTargetWarps = 6LL * 152 * kDiagWarps;
+    static_assert(kTargetWarps <= (long long)kDiagBlocks * kDiagWarps, "scratch rows");
+    long long nseg = kTargetWarps / d.nstrips;
     if (nseg > g.ny) nseg = g.ny;
     if (nseg < 1) nseg = 1;
     d.seglen = (int)((g.ny + nseg - 1) / nseg);
     d.nseg = (int)((g.ny + d.seglen - 1) / d.seglen);
     d.nunits = (long long)d.nstrips * d.nseg;
-    const long long warps = d.nunits < (long long)kDiagBlocks * kDiagWarps
-                                ? d.nunits
-                                : (long long)kDiagBlocks * kDiagWarps;
+    const long long warps = d.nunits < kTargetWarps ? d.nunits : kTargetWarps;
     d.nblocks = (int)((warps + kDiagWarps - 1) / kDiagWarps);
     return d;
 }
