@@ -43,7 +43,7 @@
  * |S^v_ab S^b_ab|^(1/2), eta_t = C_S Delta^2 sgn(j.omega) |j.omega|^(1/2)
  * from central differences of u and B, tau = tau0 + 3 x (backscatter
  * allowed, total resistivity kept >= 0).  les = 2 and 3 are not available
- * to ensembles or the adjoint.
+ * to the adjoint.
  */
 #ifndef LBMHD_H
 #define LBMHD_H
@@ -326,7 +326,10 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * graph of such launches.  Each run evolves bit-identically to an lbmhd_t
  * with the same parameters.  The grid-barrier wait is bounded (about one
  * second); on expiry the step reports LBMHD_ETIMEOUT at the next
- * synchronising call and every run must be re-initialised. */
+ * synchronising call and every run must be re-initialised.
+ * With les = 2 or 3 (common->les) each step is a moments pass and the step
+ * over every run's work units (one node per thread, one step per launch,
+ * no grid barrier), and the batch holds five moment planes per run. */
 typedef struct lbmhd_batch_t lbmhd_batch_t;
 
 /* Arrays of nruns entries (caller-owned, not retained).  Every run is
@@ -355,7 +358,8 @@ int lbmhd_batch_sync(lbmhd_batch_t* b);
 
 /* Work shape: vec nodes per thread (1, 2, 4; must divide every run's nx),
  * block threads per work unit (multiple of 32, <= 256), steps per
- * persistent launch (1..4096).  Results do not depend on the shape. */
+ * persistent launch (1..4096).  Results do not depend on the shape.
+ * Ensembles with les 2 or 3 take vec 1 and one step per launch only. */
 int lbmhd_batch_set_launch(lbmhd_batch_t* b, int vec, int block, int steps_per_launch);
 int lbmhd_batch_get_launch(const lbmhd_batch_t* b, int* vec, int* block, int* steps_per_launch);
 

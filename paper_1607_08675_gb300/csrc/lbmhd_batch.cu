@@ -25,20 +25,11 @@
 #include <string>
 #include <vector>
 
+#include "lbmhd_batch_run.cuh"
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
 
 namespace lbmhd {
-
-template <class R>
-struct RunDev {
-    long long off;   // element offset of the run's planes in each buffer
-    long long ps;    // plane stride (elements)
-    int nx, ny;
-    unsigned total;  // live threads of the run (nx / V * ny)
-    unsigned unit0;  // first unit of the run
-    Coll<R> c;
-};
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -134,6 +125,7 @@ struct lbmhd_batch_t {
     void* buf[2];
     void* d_runs;
     int* d_unit_run;
+    void* d_mom;  // les 2, 3: every run's five moment planes
     unsigned nunits;
     unsigned* d_bar;
     int* d_flag;
@@ -186,7 +178,9 @@ HostColl run_coll(const lbmhd_batch_t* b, int r) {
     c.tie6 = q.s6 > 0.0 ? 0 : 1;
     c.s7 = q.s7 > 0.0 ? q.s7 : 0.0;
     c.s8 = q.s8 > 0.0 ? q.s8 : 0.0;
-    c.les = q.les;
+    c.les = q.les == 1 ? 1 : 0;
+    c.kin = q.les >= 2 ? q.les : 0;
+    c.d2 = q.delta * q.delta;
     c.scale = (float)q.fp16_scale;
     c.inv_scale = (float)(1.0 / q.fp16_scale);
     return c;
@@ -232,9 +226,12 @@ int upload_runs_t(lbmhd_batch_t* b) {
     std::vector<RunDev<R>> rd(b->nruns);
     std::vector<int> map;
     unsigned unit = 0;
+    long long moff = 0;
     for (int r = 0; r < b->nruns; ++r) {
         const HostColl hc = run_coll(b, r);
         rd[r].off = b->off[r];
+        rd[r].moff = moff;
+        moff += 5 * b->ps[r];
         rd[r].ps = b->ps[r];
         rd[r].nx = b->nx[r];
         rd[r].ny = b->ny[r];
@@ -280,6 +277,18 @@ int configure(lbmhd_batch_t* b) {
 }
 
 cudaError_t launch_batch(lbmhd_batch_t* b, int nsteps, int parity) {
+    if (b->p.les >= 2) {  // kinetic closures: moments pass + step per step
+        const HostColl hc = run_coll(b, 0);
+        for (int s = 0; s < nsteps; ++s) {
+            const bool odd = ((parity + s) & 1) != 0;
+            const cudaError_t e = launch_batch_kinetic(
+                b->p.precision, hc.kin, b->d_runs, b->d_unit_run, b->nunits, b->block,
+                odd ? b->buf[1] : b->buf[0], odd ? b->buf[0] : b->buf[1], b->d_mom,
+                hc.inv_scale, b->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const void* k = pick_kernel(b->p.precision, b->vec);
     const HostColl hc = run_coll(b, 0);
     void* bufA = b->buf[0];
@@ -451,8 +460,6 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
         total_cells += (long long)nx[r] * ny[r];
     }
     if (total_cells > (1LL << 31)) return bfail(LBMHD_EINVAL, "ensemble exceeds 2^31 nodes");
-    if (common->les >= 2)
-        return bfail(LBMHD_EINVAL, "ensembles support les 0 and 1 (not les 2 or 3)");
 
     lbmhd_batch_t* b = new (std::nothrow) lbmhd_batch_t();
     if (!b) return bfail(LBMHD_ENOMEM, "host allocation failed");
@@ -508,6 +515,18 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
     b->buf[1] = mem[1];
     b->d_bar = (unsigned*)mem[2];
     b->d_flag = (int*)mem[3];
+    if (common->les >= 2) {
+        long long mplanes = 0;
+        for (int r = 0; r < nruns; ++r) mplanes += 5 * b->ps[r];
+        const size_t rb =
+            common->precision == LBMHD_FP64 || common->precision == LBMHD_FF ? 8 : 4;
+        e = cudaMalloc(&b->d_mom, (size_t)mplanes * rb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            lbmhd_batch_destroy(b);
+            return bfail(LBMHD_ENOMEM, "device allocation failed (ensemble moment planes)");
+        }
+    }
     cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
     cudaMemset(b->d_flag, 0, sizeof(int));
     // default shape: the widest vector dividing every run's nx, 64 threads
@@ -521,6 +540,11 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
     b->vec = v;
     b->block = v == 4 ? 64 : 128;
     b->spl = 8;
+    if (common->les >= 2) {  // kinetic closures: one node per thread, one step per launch
+        b->vec = 1;
+        b->block = 128;
+        b->spl = 1;
+    }
     int rc = configure(b);
     if (rc) {
         lbmhd_batch_destroy(b);
@@ -540,6 +564,8 @@ int lbmhd_batch_set_launch(lbmhd_batch_t* b, int vec, int block, int steps_per_l
         return bfail(LBMHD_EINVAL, "block must be a multiple of 32 in [32, 256]");
     if (steps_per_launch < 1 || steps_per_launch > 4096)
         return bfail(LBMHD_EINVAL, "steps_per_launch must be in [1, 4096]");
+    if (b->p.les >= 2 && (vec != 1 || steps_per_launch != 1))
+        return bfail(LBMHD_EINVAL, "les 2, 3 ensembles: vec 1 and one step per launch");
     LBMHD_BCK(b, cudaStreamSynchronize(b->stream));
     b->vec = vec;
     b->block = block;
@@ -776,6 +802,7 @@ void lbmhd_batch_destroy(lbmhd_batch_t* b) {
     cudaFree(b->buf[1]);
     cudaFree(b->d_runs);
     cudaFree(b->d_unit_run);
+    cudaFree(b->d_mom);
     cudaFree(b->d_bar);
     cudaFree(b->d_flag);
     if (b->own_stream) cudaStreamDestroy(b->stream);

@@ -15,6 +15,7 @@
 // This file is compiled without FMA contraction (-fmad=false), so that the
 // two kernels, whose code is shaped differently, round every operation the
 // same way and give the same bits.
+#include "lbmhd_batch_run.cuh"
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
 
@@ -24,40 +25,111 @@ namespace {
 
 __device__ __forceinline__ int wrapk(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// One node of the moments pass: rho, jx, jy, Bx, By of the populations
+// streamed into node `node` (pull + sums), into the five planes of mom.
+template <int P>
+__device__ __forceinline__ void kin_moments_node(const typename Fmt<P>::S* __restrict__ src,
+                                                 typename Fmt<P>::R* __restrict__ mom, int nx,
+                                                 int ny, long long ps, long long node,
+                                                 float inv_s) {
+    using R = typename Fmt<P>::R;
+    const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
+    R d[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p)
+        d[p] = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
+                               wrapk(x - plane_cx(p), nx)],
+                           p, 1.0f);
+    R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    R bx = (d[9] + d[11]) + (d[13] + d[15]) + d[17];
+    R by = (d[10] + d[12]) + (d[14] + d[16]) + d[18];
+    if (Fmt<P>::kScaled) {  // stored values carry the FP16 storage scale
+        drho *= (R)inv_s;
+        jx *= (R)inv_s;
+        jy *= (R)inv_s;
+        bx *= (R)inv_s;
+        by *= (R)inv_s;
+    }
+    mom[node] = R(1) + drho;
+    mom[ps + node] = jx;
+    mom[2 * ps + node] = jy;
+    mom[3 * ps + node] = bx;
+    mom[4 * ps + node] = by;
+}
+
+// One node of the step: pull, central differences of the moment planes at
+// x +- 1, y +- 1, then the filtered-equilibrium collision (MODE 2) or the
+// cross-helicity closure's relaxation times (MODE 3).
+template <int P, int MODE>
+__device__ __forceinline__ void kin_step_node(const typename Fmt<P>::S* __restrict__ src,
+                                              typename Fmt<P>::S* __restrict__ dst,
+                                              const typename Fmt<P>::R* __restrict__ mom, int nx,
+                                              int ny, long long ps, long long node,
+                                              const Coll<typename Fmt<P>::R>& c) {
+    using R = typename Fmt<P>::R;
+    const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
+    R d[9], g[10];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const R v = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
+                                    wrapk(x - plane_cx(p), nx)],
+                                p, 1.0f);
+        if (p < 9) d[p] = v;
+        else g[p - 9] = v;
+    }
+    const long long xp = (long long)y * nx + wrapk(x + 1, nx);
+    const long long xm = (long long)y * nx + wrapk(x - 1, nx);
+    const long long yp = (long long)wrapk(y + 1, ny) * nx + x;
+    const long long ym = (long long)wrapk(y - 1, ny) * nx + x;
+    if (MODE == 2) {
+        R fld[5], gx[5], gy[5], sh[4];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const R* m = mom + q * ps;
+            fld[q] = m[node];
+            gx[q] = R(0.5) * (m[xp] - m[xm]);
+            gy[q] = R(0.5) * (m[yp] - m[ym]);
+        }
+        filtered_shift<R>(fld, gx, gy, c.d2, sh);
+        if (Fmt<P>::kScaled)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
+        collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
+    } else {
+        // u = j / rho at the four neighbours, B as stored
+        const R* m0 = mom;
+        const R ixp = recip(m0[xp]), ixm = recip(m0[xm]), iyp = recip(m0[yp]),
+                iym = recip(m0[ym]);
+        R gu[2][2], gb[2][2], taus[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const R* mj = mom + (1 + a) * ps;
+            const R* mb = mom + (3 + a) * ps;
+            gu[a][0] = R(0.5) * (mj[xp] * ixp - mj[xm] * ixm);
+            gu[a][1] = R(0.5) * (mj[yp] * iyp - mj[ym] * iym);
+            gb[a][0] = R(0.5) * (mb[xp] - mb[xm]);
+            gb[a][1] = R(0.5) * (mb[yp] - mb[ym]);
+        }
+        carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
+        collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[i * ps + node] = Fmt<P>::enc(d[i], i, 1.0f);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) dst[(9 + q) * ps + node] = Fmt<P>::enc(g[q], 9 + q, 1.0f);
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) kin_moments_kernel(const typename Fmt<P>::S* __restrict__ src,
                                                           typename Fmt<P>::R* __restrict__ mom,
                                                           int nx, int ny, long long ps,
                                                           float inv_s) {
-    using R = typename Fmt<P>::R;
     const long long n = (long long)nx * ny;
     for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
-         node += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
-        R d[kPlanes];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p)
-            d[p] = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
-                                   wrapk(x - plane_cx(p), nx)],
-                               p, 1.0f);
-        R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-        R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-        R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-        R bx = (d[9] + d[11]) + (d[13] + d[15]) + d[17];
-        R by = (d[10] + d[12]) + (d[14] + d[16]) + d[18];
-        if (Fmt<P>::kScaled) {  // stored values carry the FP16 storage scale
-            drho *= (R)inv_s;
-            jx *= (R)inv_s;
-            jy *= (R)inv_s;
-            bx *= (R)inv_s;
-            by *= (R)inv_s;
-        }
-        mom[node] = R(1) + drho;
-        mom[ps + node] = jx;
-        mom[2 * ps + node] = jy;
-        mom[3 * ps + node] = bx;
-        mom[4 * ps + node] = by;
-    }
+         node += (long long)gridDim.x * blockDim.x)
+        kin_moments_node<P>(src, mom, nx, ny, ps, node, inv_s);
 }
 
 template <int P, int MODE>
@@ -66,61 +138,10 @@ __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S*
                                                        const typename Fmt<P>::R* __restrict__ mom,
                                                        int nx, int ny, long long ps,
                                                        Coll<typename Fmt<P>::R> c) {
-    using R = typename Fmt<P>::R;
     const long long n = (long long)nx * ny;
     for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
-         node += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
-        R d[9], g[10];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) {
-            const R v = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
-                                        wrapk(x - plane_cx(p), nx)],
-                                    p, 1.0f);
-            if (p < 9) d[p] = v;
-            else g[p - 9] = v;
-        }
-        const long long xp = (long long)y * nx + wrapk(x + 1, nx);
-        const long long xm = (long long)y * nx + wrapk(x - 1, nx);
-        const long long yp = (long long)wrapk(y + 1, ny) * nx + x;
-        const long long ym = (long long)wrapk(y - 1, ny) * nx + x;
-        if (MODE == 2) {
-            R fld[5], gx[5], gy[5], sh[4];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const R* m = mom + q * ps;
-                fld[q] = m[node];
-                gx[q] = R(0.5) * (m[xp] - m[xm]);
-                gy[q] = R(0.5) * (m[yp] - m[ym]);
-            }
-            filtered_shift<R>(fld, gx, gy, c.d2, sh);
-            if (Fmt<P>::kScaled)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
-            collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
-        } else {
-            // u = j / rho at the four neighbours, B as stored
-            const R* m0 = mom;
-            const R ixp = recip(m0[xp]), ixm = recip(m0[xm]), iyp = recip(m0[yp]),
-                    iym = recip(m0[ym]);
-            R gu[2][2], gb[2][2], taus[2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const R* mj = mom + (1 + a) * ps;
-                const R* mb = mom + (3 + a) * ps;
-                gu[a][0] = R(0.5) * (mj[xp] * ixp - mj[xm] * ixm);
-                gu[a][1] = R(0.5) * (mj[yp] * iyp - mj[ym] * iym);
-                gb[a][0] = R(0.5) * (mb[xp] - mb[xm]);
-                gb[a][1] = R(0.5) * (mb[yp] - mb[ym]);
-            }
-            carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
-            collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * ps + node] = Fmt<P>::enc(d[i], i, 1.0f);
-#pragma unroll
-        for (int q = 0; q < 10; ++q) dst[(9 + q) * ps + node] = Fmt<P>::enc(g[q], 9 + q, 1.0f);
-    }
+         node += (long long)gridDim.x * blockDim.x)
+        kin_step_node<P, MODE>(src, dst, mom, nx, ny, ps, node, c);
 }
 
 // ---- fused one-pass variant -------------------------------------------------
@@ -295,6 +316,48 @@ cudaError_t launch_fused(const void* src, void* dst, const Geom& g, const HostCo
     return cudaGetLastError();
 }
 
+// ---- ensembles -------------------------------------------------------------
+// One CTA per work unit of an ensemble (a unit belongs to one run; the
+// ensemble's unit map gives the run), one node per thread: the moments pass
+// and the step of the two-pass kernels, node for node, so every run evolves
+// bit-identically to its own lattice.
+template <int P>
+__global__ void __launch_bounds__(256) batch_kin_moments_kernel(
+    const RunDev<typename Fmt<P>::R>* __restrict__ runs, const int* __restrict__ unit_run,
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::R* __restrict__ mom, float inv_s) {
+    const RunDev<typename Fmt<P>::R>& rd = runs[unit_run[blockIdx.x]];
+    const unsigned t = (blockIdx.x - rd.unit0) * blockDim.x + threadIdx.x;
+    if (t < rd.total) kin_moments_node<P>(src + rd.off, mom + rd.moff, rd.nx, rd.ny, rd.ps, t, inv_s);
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) batch_kin_step_kernel(
+    const RunDev<typename Fmt<P>::R>* __restrict__ runs, const int* __restrict__ unit_run,
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst,
+    const typename Fmt<P>::R* __restrict__ mom) {
+    const RunDev<typename Fmt<P>::R>& rd = runs[unit_run[blockIdx.x]];
+    const unsigned t = (blockIdx.x - rd.unit0) * blockDim.x + threadIdx.x;
+    if (t < rd.total)
+        kin_step_node<P, MODE>(src + rd.off, dst + rd.off, mom + rd.moff, rd.nx, rd.ny, rd.ps, t,
+                               rd.c);
+}
+
+template <int P>
+cudaError_t launch_batch_p(int kin, const void* runs, const int* unit_run, unsigned nunits,
+                           int block, const void* src, void* dst, void* mom, float inv_s,
+                           cudaStream_t st) {
+    using S = typename Fmt<P>::S;
+    using R = typename Fmt<P>::R;
+    const RunDev<R>* rd = (const RunDev<R>*)runs;
+    batch_kin_moments_kernel<P><<<nunits, block, 0, st>>>(rd, unit_run, (const S*)src, (R*)mom,
+                                                          inv_s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto step = kin == 3 ? batch_kin_step_kernel<P, 3> : batch_kin_step_kernel<P, 2>;
+    step<<<nunits, block, 0, st>>>(rd, unit_run, (const S*)src, (S*)dst, (const R*)mom);
+    return cudaGetLastError();
+}
+
 unsigned kin_grid(long long n) {
     long long b = (n + 255) / 256;
     return (unsigned)(b < 1 ? 1 : (b > 65535LL * 8 ? 65535LL * 8 : b));
@@ -317,6 +380,21 @@ cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const
 }
 
 }  // namespace
+
+cudaError_t launch_batch_kinetic(int prec, int kin, const void* runs, const int* unit_run,
+                                 unsigned nunits, int block, const void* src, void* dst,
+                                 void* mom, float inv_s, cudaStream_t st) {
+    switch (prec) {
+        case P_FP64: return launch_batch_p<P_FP64>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+        case P_FP32: return launch_batch_p<P_FP32>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+        case P_FP32_DEV:
+            return launch_batch_p<P_FP32_DEV>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+        case P_FP16_DEV:
+            return launch_batch_p<P_FP16_DEV>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+        case P_FF: return launch_batch_p<P_FF>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
                                 void* dst, void* mom, const Geom& g, const HostColl& c,

@@ -169,3 +169,42 @@ def test_batch_rejects_bad_runs(L):
     with pytest.raises(L.LBMHDError):
         L.lbmhd_batch_init(b, 5, *inputs.orszag_tang(128, 64))
     L.lbmhd_batch_destroy(b)
+
+
+@pytest.mark.parametrize("les", [2, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp16_dev", "fp64", "ff"])
+def test_kinetic_ensemble_runs_equal_single_lattices_bitwise(L, prec, les):
+    """Ensembles of the paper's kinetic LES (les 2) and of the cross-helicity
+    closure (les 3): a moments pass and the step over every run's work units
+    per step, the two-pass kernels' per-node code, so every run equals its
+    own lattice bit for bit, through graph replays and a direct tail.  The
+    shape is one node per thread and one step per launch; others are
+    refused."""
+    nx, ny, tn, te, cs = zip(*RUNS)
+    common = L.lbmhd_params_default(precision=prec, les=les, delta=2.0)
+    b = L.lbmhd_batch_create(nx, ny, tn, te, cs, common)
+    vec, block, spl = L.lbmhd_batch_get_launch(b)
+    assert vec == 1 and spl == 1
+    for bad in ((2, 64, 1), (1, 64, 8)):
+        with pytest.raises(L.LBMHDError):
+            L.lbmhd_batch_set_launch(b, *bad)
+    if prec == "fp32":  # the autotuner keeps to the allowed shapes
+        assert L.lbmhd_batch_autotune(b, None, 4) > 0
+        vec, block, spl = L.lbmhd_batch_get_launch(b)
+        assert vec == 1 and spl == 1
+    L.lbmhd_batch_set_launch(b, 1, 64, 1)
+    fields = [inputs.orszag_tang(r[0], r[1], seed=20 + i) for i, r in enumerate(RUNS)]
+    for i, f in enumerate(fields):
+        L.lbmhd_batch_init(b, i, *f)
+    steps = 70
+    L.lbmhd_batch_step(b, steps)
+    assert L.lbmhd_batch_step_count(b) == steps
+    for i, (rx, ry, rtn, rte, rcs) in enumerate(RUNS):
+        h = L.lbmhd_create(rx, ry, L.lbmhd_params_default(
+            precision=prec, les=les, delta=2.0, tau_nu=rtn, tau_eta=rte, C_S=rcs))
+        L.lbmhd_init(h, *fields[i])
+        L.lbmhd_step(h, steps)
+        ref = L.lbmhd_get_state(h)
+        L.lbmhd_destroy(h)
+        assert np.array_equal(L.lbmhd_batch_get_state(b, i), ref), (prec, les, i)
+    L.lbmhd_batch_destroy(b)

@@ -117,7 +117,7 @@ def test_kinetic_les_graph_replay_bitwise(L, vec, per_step):
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_kinetic_les_rejected_by_adjoint_and_ensembles(L):
+def test_kinetic_les_rejected_by_the_adjoint(L):
     import torch
 
     h = L.lbmhd_create(16, 16, L.lbmhd_params_default(precision="fp64", **KW))
@@ -125,9 +125,6 @@ def test_kinetic_les_rejected_by_adjoint_and_ensembles(L):
     with pytest.raises(L.LBMHDError):
         L.lbmhd_adjoint_record(h, *f, 4, 2)
     L.lbmhd_destroy(h)
-    with pytest.raises(L.LBMHDError):
-        L.lbmhd_batch_create([16], [16], [0.6], [0.6], [0.0],
-                             L.lbmhd_params_default(precision="fp32", les=2))
 
 
 CH = dict(tau_nu=0.6, tau_eta=0.65, C_S=0.3, delta=2.0, les=3)
