@@ -359,7 +359,7 @@ def run_adjoint(args):
          for a in inputs.orszag_tang(n, n, seed=0)]
     refs = {}
     with torch.no_grad():
-        for prec in ("fp32", "fp64"):  # the reference run in the trial's precision
+        for prec in ("fp32", "ff", "fp64"):  # the reference run in the trial's precision
             refs[prec] = AG.rollout(*f, 0.12, 0.6, 0.6, steps, every=every, precision=prec)
 
     def loss_of(out, prec="fp64"):
@@ -370,7 +370,7 @@ def run_adjoint(args):
     loss_of(AG.rollout(*w, 0.1, 0.6, 0.6, 2 * every, every=every, precision="fp32"),
             "fp32").backward()
     res = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "ff", "fp64"):
         leaves = [t.clone().requires_grad_(True) for t in f]
         th = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (0.1, 0.6, 0.6)]
         torch.cuda.synchronize()
@@ -395,10 +395,12 @@ def run_adjoint(args):
     r64, r32 = res["fp64"], res["fp32"]
     return {"workload": f"Orszag-Tang {n}x{n}, {steps} steps, checkpoints every {every}, "
                         "loss vs C_S = 0.12 run",
-            "fp32": r32, "fp64": r64, "fd_dC_S": fd,
+            "fp32": r32, "ff": res["ff"], "fp64": r64, "fd_dC_S": fd,
             "fd_rel_err_fp64": abs(r64["dC_S"] - fd) / abs(fd),
             "fp32_vs_fp64_rel": {k: abs(r32[k] - r64[k]) / abs(r64[k])
                                  for k in ("dC_S", "dtau_nu", "dtau_eta", "du0_norm", "dB0_norm")},
+            "ff_vs_fp64_rel": {k: abs(res["ff"][k] - r64[k]) / abs(r64[k])
+                               for k in ("dC_S", "dtau_nu", "dtau_eta", "du0_norm", "dB0_norm")},
             "node_steps_per_s_fp32": n * n * steps / (r32["forward_s"] + r32["backward_s"])}
 
 

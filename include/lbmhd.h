@@ -288,7 +288,7 @@ int lbmhd_ff_eval(int op, const double* x, const double* y, double* out, long lo
  * Gradients of a scalar function of the final moments with respect to
  * C_S, tau_nu, tau_eta and the initial fields, through the exact transpose
  * of the discrete step (pull-stream and the collision of Sec. 3 with the
- * local Smagorinsky rates).  Supported storage: FP64, FP32, FP32_DEV.  The
+ * local Smagorinsky rates).  Supported storage: FP64, FF, FP32, FP32_DEV.  The
  * derivative of |x| and of sqrt at 0 (local |S|, |j| of exactly zero) is
  * taken as 0. */
 

@@ -41,6 +41,17 @@ namespace lbmhd {
 // Reverse-mode derivative of collide<R> at the pulled node state (d, g):
 // given the adjoint (ld, lg) of the outputs, returns the adjoint (md, mg)
 // of the inputs and th = d/d(tau_nu, tau_eta, k18, k36) of lambda . C.
+// a / b in the arithmetic type: IEEE division for float and double, the
+// double-word reciprocal for double-word; and a value as FP64.
+template <class R>
+__device__ __forceinline__ R quot(R a, R b) {
+    return a / b;
+}
+__device__ __forceinline__ ff quot(ff a, ff b) { return a * rcp(b); }
+__device__ __forceinline__ double to_f64(float v) { return v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(ff v) { return (double)v.hi + (double)v.lo; }
+
 template <class R>
 __device__ __forceinline__ void collide_adjoint(const R (&d)[9], const R (&g)[10],
                                                 const R (&ld)[9], const R (&lg)[10],
@@ -140,7 +151,7 @@ __device__ __forceinline__ void collide_adjoint(const R (&d)[9], const R (&g)[10
     if (c.les) {
         // tau_m = (te + sqrt(te^2 + k36 J)) / 2
         teb += R(0.5) * taumb;
-        const R Bb = taumb * R(0.25) / rB;
+        const R Bb = quot(taumb * R(0.25), rB);
         teb += Bb * R(2) * c.te;
         k36b += Bb * J;
         const R Jb = Bb * c.k36;
@@ -152,14 +163,14 @@ __device__ __forceinline__ void collide_adjoint(const R (&d)[9], const R (&g)[10
         Eb -= R(2) * Xb;
         // tau_e = (tn + sqrt(tn^2 + k18 Q / rho)) / 2
         tnb += R(0.5) * taueb;
-        const R Ab = taueb * R(0.25) / rA;
+        const R Ab = quot(taueb * R(0.25), rA);
         tnb += Ab * R(2) * c.tn;
         k18b += Ab * Q * irho;
         const R Qb = Ab * c.k18 * irho;
         irhob += Ab * c.k18 * Q;
         if (Q > R(0)) {
-            nb4 += Qb * n4 / Q;
-            nb3 += Qb * R(4) * n3 / Q;
+            nb4 += quot(Qb * n4, Q);
+            nb3 += quot(Qb * R(4) * n3, Q);
         }
     } else {
         tnb += taueb;
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
     const long long n = (long long)nx * ny;
     // per-thread sensitivity sums: FP64 for FP64 storage; double-word for
     // the FP32 forms, which keeps FP64 instructions out of the node loop
-    using Acc = typename std::conditional<sizeof(R) == 8, double, ff>::type;
+    using Acc = typename std::conditional<std::is_same<R, double>::value, double, ff>::type;
     Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
     for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
          node += (long long)gridDim.x * blockDim.x) {
@@ -279,8 +290,8 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if constexpr (sizeof(R) == 8) acc[q] += th[q];
-            else dw_accumulate(acc[q], th[q]);
+            if constexpr (std::is_same<R, float>::value) dw_accumulate(acc[q], th[q]);
+            else acc[q] += th[q];
         }
     }
     __shared__ double red[kAdjBlock / 32][4];
@@ -288,8 +299,7 @@ __global__ void __launch_bounds__(kAdjBlock) adj_step_kernel(
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         double a;
-        if constexpr (sizeof(R) == 8) a = acc[q];
-        else a = (double)acc[q].hi + (double)acc[q].lo;
+        a = to_f64(acc[q]);
         const double w = warp_sum_d(a);
         if (lane == 0) red[warp][q] = w;
     }
@@ -337,7 +347,7 @@ __global__ void adj_seed_kernel(const typename Fmt<P>::S* __restrict__ x,
         double d[9], drho = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            d[i] = (double)Fmt<P>::dec(x[i * ps + node], i, inv_scale);
+            d[i] = to_f64(Fmt<P>::dec(x[i * ps + node], i, inv_scale));
             drho += d[i];
         }
         const double jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
@@ -373,7 +383,7 @@ __global__ void adj_init_kernel(const R* __restrict__ lam, const double* __restr
         double gr = 0.0, gu = 0.0, gv = 0.0, gbx = 0.0, gby = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double l = (double)lam[i * ps + node];
+            const double l = to_f64(lam[i * ps + node]);
             const double cx = plane_cx(i), cy = plane_cy(i), w = plane_rest<double>(i);
             const double cu = cx * u + cy * v, cb = cx * Bx + cy * By, c2 = cx * cx + cy * cy;
             gr += l * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
@@ -385,7 +395,7 @@ __global__ void adj_init_kernel(const R* __restrict__ lam, const double* __restr
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const int p = 9 + 2 * k;
-            const double lx = (double)lam[p * ps + node], ly = (double)lam[(p + 1) * ps + node];
+            const double lx = to_f64(lam[p * ps + node]), ly = to_f64(lam[(p + 1) * ps + node]);
             const double Cx = plane_cx(p), Cy = plane_cy(p), wk = k == 0 ? 1.0 / 3.0 : 1.0 / 6.0;
             const double Cu = Cx * u + Cy * v, CB = Cx * Bx + Cy * By;
             // g_x = wk (Bx + 3 (Cu Bx - CB u)), g_y = wk (By + 3 (Cu By - CB v))
@@ -492,8 +502,8 @@ int lbmhd_adjoint_record(lbmhd_t* h, const double* rho0, const double* ux0, cons
     if (!rho0 || !ux0 || !uy0 || !bx0 || !by0) return afail(LBMHD_EINVAL, "NULL field");
     if (nsteps < 1 || every < 1) return afail(LBMHD_EINVAL, "nsteps and every must be >= 1");
     const int prec = h->p.precision;
-    if (prec != LBMHD_FP64 && prec != LBMHD_FP32 && prec != LBMHD_FP32_DEV)
-        return afail(LBMHD_EINVAL, "the adjoint supports FP64, FP32 and FP32_DEV storage");
+    if (prec != LBMHD_FP64 && prec != LBMHD_FP32 && prec != LBMHD_FP32_DEV && prec != LBMHD_FF)
+        return afail(LBMHD_EINVAL, "the adjoint supports FP64, FF, FP32 and FP32_DEV storage");
     if (h->p.les >= 2)
         return afail(LBMHD_EINVAL, "the adjoint supports les 0 and 1 (not les 2 or 3)");
     free_tape(h);
@@ -544,7 +554,7 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
     const int prec = h->p.precision;
     const long long n = (long long)h->geom.nx * h->geom.ny;
     const size_t sb = storage_bytes(prec);
-    const size_t rb = prec == LBMHD_FP64 ? sizeof(double) : sizeof(float);
+    const size_t rb = prec == LBMHD_FP64 || prec == LBMHD_FF ? 8 : sizeof(float);
     const size_t plane_bytes_s = (size_t)kNumPlanes * h->geom.ps * sb;
     const size_t plane_bytes_r = (size_t)kNumPlanes * h->geom.ps * rb;
     char* seg = nullptr;
@@ -582,6 +592,7 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
     if (e == cudaSuccess) {
         switch (prec) {
             case LBMHD_FP64: e = run_seed<P_FP64>(h, h->buf[h->cur], gin, lcur); break;
+            case LBMHD_FF: e = run_seed<P_FF>(h, h->buf[h->cur], gin, lcur); break;
             case LBMHD_FP32: e = run_seed<P_FP32>(h, h->buf[h->cur], gin, lcur); break;
             default: e = run_seed<P_FP32_DEV>(h, h->buf[h->cur], gin, lcur); break;
         }
@@ -601,6 +612,7 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
             const void* x = seg + (size_t)j * plane_bytes_s;
             switch (prec) {
                 case LBMHD_FP64: e = run_adj_step<P_FP64>(h, x, lcur, lnext, partials); break;
+                case LBMHD_FF: e = run_adj_step<P_FF>(h, x, lcur, lnext, partials); break;
                 case LBMHD_FP32: e = run_adj_step<P_FP32>(h, x, lcur, lnext, partials); break;
                 default: e = run_adj_step<P_FP32_DEV>(h, x, lcur, lnext, partials); break;
             }
@@ -614,6 +626,10 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
         if (prec == LBMHD_FP64)
             adj_init_kernel<double><<<adj_grid(n), kAdjBlock, 0, h->stream>>>(
                 (const double*)lcur, t->fields, d_rho0, d_ux0, d_uy0, d_bx0, d_by0, h->geom.nx,
+                h->geom.ny, h->geom.ps);
+        else if (prec == LBMHD_FF)
+            adj_init_kernel<ff><<<adj_grid(n), kAdjBlock, 0, h->stream>>>(
+                (const ff*)lcur, t->fields, d_rho0, d_ux0, d_uy0, d_bx0, d_by0, h->geom.nx,
                 h->geom.ny, h->geom.ps);
         else
             adj_init_kernel<float><<<adj_grid(n), kAdjBlock, 0, h->stream>>>(

@@ -170,3 +170,46 @@ def test_adjoint_errors(env):
         L.lbmhd_adjoint_backward(h, [None] * 5)
     assert e.value.code == -7
     L.lbmhd_destroy(h)
+
+
+# Double-word (FF) adjoint: the FP64 bars scaled by the ratio of the unit
+# roundoffs, 2^-48 / 2^-53 = 32.
+FF_RATIO = 2.0 ** 5
+
+
+@pytest.mark.parametrize("rates", [None, MRT])
+def test_ff_adjoint_equals_tape_oracle(env, rates):
+    """Double-word storage and adjoint against the brute-force FP64 tape
+    oracle: the FP64 adjoint's 1e-10 bar times 32."""
+    from oracle import tape
+
+    L, _, torch = env
+    fields = inputs.orszag_tang(16, 16, seed=2, amp=1e-3)
+    rng = np.random.default_rng(3)
+    weights = [rng.standard_normal((16, 16)) for _ in range(5)]
+    th = (0.15, 0.6, 0.65)
+    steps = 20
+    kw = {} if rates is None else dict(rates=(rates["s5"], rates["s6"], rates["s7"], rates["s8"]))
+    _, ref = tape.gradients(fields, th[1], th[2], th[0], steps, weights, **kw)
+    dth, df = adjoint(L, torch, fields, weights, th, steps, 7, prec="ff", rates=rates)
+    for got, key in zip(dth, ("C_S", "tau_nu", "tau_eta")):
+        assert abs(got - ref[key]) <= FF_RATIO * 1e-10 * abs(ref[key]), (key, got, ref[key])
+    for got, key in zip(df, ("rho0", "ux0", "uy0", "bx0", "by0")):
+        scale = np.max(np.abs(ref[key]))
+        assert np.max(np.abs(got - ref[key])) <= FF_RATIO * 1e-10 * scale, key
+
+
+def test_ff_adjoint_against_fp64_adjoint(env):
+    """On the 64^2 case of the FP32 comparison: the double-word adjoint sits
+    with FP64 (3.2e-9), orders of magnitude below FP32's 5e-3."""
+    L, _, torch = env
+    n = 64
+    fields = inputs.orszag_tang(n, n, seed=8)
+    rng = np.random.default_rng(6)
+    weights = [rng.standard_normal((n, n)) for _ in range(5)]
+    th = (0.1, 0.6, 0.6)
+    d64, f64 = adjoint(L, torch, fields, weights, th, 100, 25, rates=MRT)
+    dff, fff = adjoint(L, torch, fields, weights, th, 100, 25, prec="ff", rates=MRT)
+    assert np.max(np.abs(dff - d64) / np.abs(d64)) < FF_RATIO * 1e-10, (dff, d64)
+    for a, b in zip(fff, f64):
+        assert np.max(np.abs(a - b)) < FF_RATIO * 1e-10 * np.max(np.abs(b))
