@@ -78,8 +78,8 @@ typedef enum {
     LBMHD_FF = 4        /* double-word deviations: each value an FP32 pair
                            (hi, lo), 8 bytes, 48-bit significand; arithmetic
                            in double-word on the FP32 units (unit roundoff
-                           2^-48 against FP64's 2^-53).  No adjoint; TMA
-                           variant not available. */
+                           2^-48 against FP64's 2^-53).  TMA variant not
+                           available. */
 } lbmhd_precision;
 
 typedef struct lbmhd_t lbmhd_t;
