@@ -3,6 +3,8 @@
 #include "lbmhd_device.cuh"
 #include "lbmhd_internal.h"
 
+#include <type_traits>
+
 namespace lbmhd {
 
 // ---- FP64 views of a stored value ---------------------------------------
@@ -156,10 +158,10 @@ __global__ void finite_kernel(const typename Fmt<P>::S* __restrict__ st, int* fl
 }
 
 // ---- diagnostics ----------------------------------------------------------
-// Each block walks tiles of 32 x 8 nodes in a fixed order.  A tile's node
-// moments (and a one-node periodic halo) are staged in shared memory, so
-// the central differences of omega, j_z and div B read neighbours from
-// there.  The per-node arithmetic runs in the format's arithmetic type R,
+// Warps sweep column strips down the lattice (the work split below), so the
+// central differences of omega, j_z and div B take x-neighbours from lane
+// shuffles and y-neighbours from the rows kept in registers.  The per-node
+// arithmetic runs in the format's arithmetic type R,
 // as in the step kernels: FP32 for the FP32 and FP16 storage forms, FP64
 // for FP64 storage, double-word for FF.  Each thread sums its nodes in an
 // accumulator type A -- FP64 for FP64 storage, double-word (48-bit
@@ -250,42 +252,98 @@ __device__ __forceinline__ ff shfl_dn_r(ff v) { return ff(shfl_dn_r(v.hi), shfl_
 // Work split: a warp sweeps a strip of kOwn columns down a segment of rows.
 // Lane l holds column x0 - 1 + l (periodic): lanes 1..sw own the strip's
 // columns, lanes 0 and sw + 1 the halo columns whose moments the owners'
-// x-differences need; rows y - 1, y, y + 1 stay in registers as the warp
-// moves down, so every node's moments are formed once (plus the halo
-// columns and two rows per segment) from the 19 values stored at it -- no
-// shared memory, no barrier.
+// x-differences need; the moments of rows y - 1, y, y + 1 stay in
+// registers as the warp moves down, so every node's moments are formed once
+// (plus the halo columns and two rows per segment) from the 19 values
+// stored at it.  No barrier: a warp's stored values pass through its own
+// ring of rows (below).
 struct DiagPlan {
     int nstrips, nseg, seglen, nblocks;
     long long nunits;
 };
-inline DiagPlan diag_plan(const Geom& g) {
+// The work is cut into units of one warp each, a whole number of waves of
+// the kernel's resident warps and at least kDiagMinWarps warps per SM (the
+// fastest split at 8192^2 for every ring depth and residency tried: fewer
+// warps leave the memory system short of requests, a part-filled last
+// wave leaves SMs idle).
+constexpr int kDiagMinWarps = 48;
+inline DiagPlan diag_plan(const Geom& g, long long resident_warps, int nsm) {
     DiagPlan d;
     d.nstrips = (g.nx + kOwn - 1) / kOwn;
-    // about three full waves on GB300 (152 SMs, two blocks of 256 threads
-    // resident each): 912 blocks, within the kDiagBlocks scratch rows
-    constexpr long long kTargetWarps = 6LL * 152 * kDiagWarps;
-    static_assert(kTargetWarps <= (long long)kDiagBlocks * kDiagWarps, "scratch rows");
-    long long nseg = kTargetWarps / d.nstrips;
+    const long long want = (long long)kDiagMinWarps * nsm;
+    const long long cap = (long long)kDiagBlocks * kDiagWarps;  // partial rows
+    long long target = cap;
+    if (resident_warps < cap) {
+        long long waves = (want + resident_warps - 1) / resident_warps;
+        if (waves * resident_warps > cap) waves = cap / resident_warps;  // whole waves only
+        target = waves * resident_warps;
+    }
+    if (target < kDiagWarps) target = kDiagWarps;
+    long long nseg = target / d.nstrips;
     if (nseg > g.ny) nseg = g.ny;
     if (nseg < 1) nseg = 1;
     d.seglen = (int)((g.ny + nseg - 1) / nseg);
     d.nseg = (int)((g.ny + d.seglen - 1) / d.seglen);
     d.nunits = (long long)d.nstrips * d.nseg;
-    const long long warps = d.nunits < kTargetWarps ? d.nunits : kTargetWarps;
+    const long long warps = d.nunits < target ? d.nunits : target;
     d.nblocks = (int)((warps + kDiagWarps - 1) / kDiagWarps);
     return d;
 }
 
-// Two-byte FP16 values are not worth a prefetch register set (measured
-// faster without: 0.94 ms vs 1.15 ms at 8192^2).
+// Rows of stored values in flight per warp.  4- and 8-byte values are
+// staged by asynchronous copies (cp.async) into a per-warp ring of
+// kDiagRing<P> rows in shared memory: the next row is in flight while a row
+// is reduced without a register set to hold it, and the kernel keeps to 64
+// registers for the FP32 forms, four blocks per SM (the sweep is bound by
+// latency; with the next row prefetched into registers it ran at 107
+// registers, two blocks per SM).
+// Lane l copies and later reads back only its own column, so its own
+// wait_group is the only synchronisation the ring needs.  Two-byte FP16
+// values are read straight into registers, one row ahead only when that
+// pays (measured faster without: 0.94 ms vs 1.15 ms at 8192^2).
+#ifndef LBMHD_DIAG_RING4
+#define LBMHD_DIAG_RING4 3
+#endif
+template <int P>
+constexpr int kDiagRing = sizeof(typename Fmt<P>::S) == 2   ? 0
+                          : sizeof(typename Fmt<P>::S) == 4 ? LBMHD_DIAG_RING4
+                                                            : 2;
+template <int P>
+constexpr size_t diag_smem_bytes() {
+    return (size_t)kDiagWarps * kDiagRing<P> * kPlanes * 32 * sizeof(typename Fmt<P>::S);
+}
+
+// One 4- or 8-byte cp.async (the L1-allocating form, the one that takes
+// sizes below 16 bytes), its commit and a wait for all but the N most
+// recent groups.
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+    static_assert(B == 4 || B == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int P>
 __global__ void __launch_bounds__(32 * kDiagWarps)
     diag_kernel(const typename Fmt<P>::S* __restrict__ st, int nx, int ny, long long ps,
                 float inv_scale, int nstrips, int seglen, long long nunits, double* partials) {
     using R = typename Fmt<P>::R;
     using A = typename DiagAcc<R>::A;
+    using S = typename Fmt<P>::S;
+    constexpr int K = kDiagRing<P>;
+    static_assert(K == 0 || K >= 2, "the ring holds rows y - 1 and y while y + 1 lands");
+    extern __shared__ __align__(16) unsigned char diag_ring_smem[];
     __shared__ double red[kDiagWarps][kNQ];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    S* ring = reinterpret_cast<S*>(diag_ring_smem) + (size_t)warp * K * kPlanes * 32 + lane;
     A acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = A(0);
@@ -301,59 +359,138 @@ __global__ void __launch_bounds__(32 * kDiagWarps)
         const bool own = lane >= 1 && lane <= sw;
         int col = x0 - 1 + (lane <= sw + 1 ? lane : 1);  // idle lanes shadow an owner
         col = col < 0 ? col + nx : (col >= nx ? col - nx : col);
-        using S = typename Fmt<P>::S;
-        auto load = [&](int y, S (&raw)[kPlanes]) {
-            int yw = y % ny;  // y in [-1, ny + 1]: more than one wrap when ny <= 2
-            if (yw < 0) yw += ny;
-            const long long o = (long long)yw * nx + col;
-#pragma unroll
-            for (int i = 0; i < kPlanes; ++i) raw[i] = st[i * ps + o];
+        // Rows are fetched in order y0 - 1, y0, y0 + 1, ...; yf is the
+        // stored row of the next one (periodic; y0 - 1 wraps more than once
+        // when ny <= 2).
+        int yf = (y0 - 1) % ny;
+        if (yf < 0) yf += ny;
+        auto fetch_ptr = [&]() {
+            const S* src = st + ((long long)yf * nx + col);
+            yf = yf + 1 == ny ? 0 : yf + 1;
+            return src;
         };
-        auto moments = [&](const S (&raw)[kPlanes], R (&m)[kNM]) {
-            node_moments_raw<P>(raw, inv_scale, m);
-        };
-        // moments of rows y - 1, y, y + 1; the stored values of row y + 2 are
-        // in flight while row y is reduced
-        R mp[kNM], mc[kNM], mn[kNM];
-        S ra[kPlanes], rb[kPlanes];
-        load(y0 - 1, ra);
-        load(y0, rb);
-        moments(ra, mp);
-        if (sizeof(S) >= 4) load(y0 + 1, ra);
-        moments(rb, mc);
-        constexpr bool kPrefetch = sizeof(S) >= 4;
-        for (int y = y0; y < y1; ++y) {
-            if (!kPrefetch) load(y + 1, ra);
-            moments(ra, mn);  // row y + 1
-            if (kPrefetch) load(y + 2, ra);
-            // x-neighbours of row y (lanes -1, +1)
-            const R vL = shfl_up_r(mc[kUy]), vR = shfl_dn_r(mc[kUy]);
-            const R bxL = shfl_up_r(mc[kBx]), bxR = shfl_dn_r(mc[kBx]);
-            const R byL = shfl_up_r(mc[kBy]), byR = shfl_dn_r(mc[kBy]);
+        // The terms of row y from the moments of rows y - 1 (a), y (b) and
+        // y + 1 (c), into partial sums g of a group of rows (assigned for
+        // the group's first row); x-neighbours from lanes -1 and +1.
+        auto row_terms = [&](const R (&a)[kNM], const R (&b)[kNM], const R (&c)[kNM],
+                             R (&g)[kNQ], bool first) {
+            const R vL = shfl_up_r(b[kUy]), vR = shfl_dn_r(b[kUy]);
+            const R bxL = shfl_up_r(b[kBx]), bxR = shfl_dn_r(b[kBx]);
+            const R byL = shfl_up_r(b[kBy]), byR = shfl_dn_r(b[kBy]);
             if (own) {
-                const R u = mc[kUx], v = mc[kUy], Bx = mc[kBx], By = mc[kBy];
-                acc_add(acc[0], mc[kDrho]);  // the node count is added at the end
-                acc_add(acc[1], mc[kJx]);
-                acc_add(acc[2], mc[kJy]);
-                acc_add(acc[3], Bx);
-                acc_add(acc[4], By);
-                acc_add(acc[5], mc[kJx] * u + mc[kJy] * v);  // rho |u|^2
-                acc_add(acc[6], Bx * Bx + By * By);
-                const R om = half * (vR - vL) - half * (mn[kUx] - mp[kUx]);
-                acc_add(acc[7], om * om);
-                acc_add(acc[8], u * Bx + v * By);
-                const R dv = half * (bxR - bxL) + half * (mn[kBy] - mp[kBy]);
+                const R u = b[kUx], v = b[kUy], Bx = b[kBx], By = b[kBy];
+                const R om = half * (vR - vL) - half * (c[kUx] - a[kUx]);
+                const R dv = half * (bxR - bxL) + half * (c[kBy] - a[kBy]);
+                const R jz = half * (byR - byL) - half * (c[kBx] - a[kBx]);
                 const R adv = fabs(dv);
                 if (gt(adv, dmax)) dmax = adv;
-                acc_add(acc[10], dv * dv);
-                const R jz = half * (byR - byL) - half * (mn[kBx] - mp[kBx]);
-                acc_add(acc[11], jz * jz);
-            }
+                const R t[kNQ] = {b[kDrho],  // the node count is added at the end
+                                  b[kJx],
+                                  b[kJy],
+                                  Bx,
+                                  By,
+                                  b[kJx] * u + b[kJy] * v,  // rho |u|^2
+                                  Bx * Bx + By * By,
+                                  om * om,
+                                  u * Bx + v * By,
+                                  R(0),  // slot 9 is the div B maximum
+                                  dv * dv,
+                                  jz * jz};
 #pragma unroll
-            for (int q = 0; q < kNM; ++q) {
-                mp[q] = mc[q];
-                mc[q] = mn[q];
+                for (int q = 0; q < kNQ; ++q)
+                    if (q != 9) g[q] = first ? t[q] : g[q] + t[q];
             }
+        };
+        // FP32 arithmetic with the ring sweeps rows in groups of three: the
+        // moments of three rows rotate through m0, m1, m2 with no copies,
+        // and each group's terms (at most two FP32 roundings per term,
+        // unbiased) are folded into the double-word accumulators once --
+        // about a third of the instructions per row go to those folds.
+        // FP64 and double-word arithmetic gain nothing from the grouping,
+        // and the FP16 form, which loads straight into registers, loses the
+        // overlap of one row's loads with the previous row's arithmetic: they
+        // fold every row.
+        constexpr int G = (std::is_same<R, float>::value && K > 0) ? 3 : 1;
+        R m0[kNM], m1[kNM], m2[kNM];
+        auto fold = [&](const R (&g)[kNQ]) {
+            if (own) {
+#pragma unroll
+                for (int q = 0; q < kNQ; ++q)
+                    if (q != 9) acc_add(acc[q], g[q]);
+            }
+        };
+        auto sweep = [&](auto&& next) {
+            next(m0);  // row y0 - 1
+            next(m1);  // row y0
+            if constexpr (G == 3) {
+                for (int y = y0; y < y1; y += 3) {
+                    R g[kNQ];
+                    next(m2);  // row y + 1
+                    row_terms(m0, m1, m2, g, true);
+                    if (y + 1 < y1) {
+                        next(m0);  // row y + 2
+                        row_terms(m1, m2, m0, g, false);
+                    }
+                    if (y + 2 < y1) {
+                        next(m1);  // row y + 3
+                        row_terms(m2, m0, m1, g, false);
+                    }
+                    fold(g);
+                }
+            } else {
+                for (int y = y0; y < y1; ++y) {
+                    R g[kNQ];
+                    next(m2);  // row y + 1
+                    row_terms(m0, m1, m2, g, true);
+                    fold(g);
+#pragma unroll
+                    for (int q = 0; q < kNM; ++q) {
+                        m0[q] = m1[q];
+                        m1[q] = m2[q];
+                    }
+                }
+            }
+        };
+        if constexpr (K > 0) {
+            // rows y0 - 1 .. y1 pass through the ring; row t (counted from
+            // y0 - 1) sits in slot t % K.  One commit group per row, empty
+            // past the last row, keeps "row t done" = "at most K - 1 groups
+            // pending".
+            const int nrows = y1 - y0 + 2;
+            auto issue = [&](int t) {
+                if (t < nrows) {
+                    const S* src = fetch_ptr();
+                    S* dst = ring + (t % K) * (kPlanes * 32);
+#pragma unroll
+                    for (int i = 0; i < kPlanes; ++i)
+                        cp_async_small<sizeof(S)>(dst + i * 32, src + i * ps);
+                }
+                cp_async_commit();
+            };
+            int tn = 0;  // the next row to take
+            auto take = [&](R (&m)[kNM]) {
+                cp_async_wait<K - 1>();
+                S raw[kPlanes];
+                const S* p = ring + (tn % K) * (kPlanes * 32);
+#pragma unroll
+                for (int i = 0; i < kPlanes; ++i) raw[i] = p[i * 32];
+                node_moments_raw<P>(raw, inv_scale, m);
+                issue(tn + K);  // the slot is free once its values are in registers
+                ++tn;
+            };
+#pragma unroll
+            for (int t = 0; t < K; ++t) issue(t);
+            sweep(take);
+            cp_async_wait<0>();
+        } else {
+            auto load = [&](R (&m)[kNM]) {
+                const S* src = fetch_ptr();
+                S raw[kPlanes];
+#pragma unroll
+                for (int i = 0; i < kPlanes; ++i) raw[i] = src[i * ps];
+                node_moments_raw<P>(raw, inv_scale, m);
+            };
+            sweep(load);
         }
     }
 #pragma unroll
@@ -471,16 +608,66 @@ cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Ge
     return cudaGetLastError();
 }
 
-int diag_num_blocks(const Geom& g) { return diag_plan(g).nblocks; }
+// Warps of diag_kernel<P> resident on the device at once (the kernel's
+// registers and ring bound its blocks per SM), found once per process.
+struct DiagOcc {
+    long long warps;  // resident warps of the kernel on the device
+    int nsm;
+};
+template <int P>
+static DiagOcc diag_occupancy() {
+    static const DiagOcc o = [] {
+        constexpr size_t smem = diag_smem_bytes<P>();
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(diag_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        int dev = 0, nsm = 0, bps = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, diag_kernel<P>, 32 * kDiagWarps, smem);
+        cudaGetLastError();  // a failed query leaves the floors below
+        nsm = nsm > 0 ? nsm : 1;
+        return DiagOcc{(long long)nsm * (bps > 0 ? bps : 1) * kDiagWarps, nsm};
+    }();
+    return o;
+}
+
+static DiagPlan diag_plan_for(const Geom& g, int prec) {
+    DiagOcc o{kDiagWarps, 1};
+    switch (prec) {
+        case P_FP64: o = diag_occupancy<P_FP64>(); break;
+        case P_FP32: o = diag_occupancy<P_FP32>(); break;
+        case P_FP32_DEV: o = diag_occupancy<P_FP32_DEV>(); break;
+        case P_FP16_DEV: o = diag_occupancy<P_FP16_DEV>(); break;
+        case P_FF: o = diag_occupancy<P_FF>(); break;
+        default: break;
+    }
+    return diag_plan(g, o.warps, o.nsm);
+}
+
+int diag_num_blocks(const Geom& g, int prec) { return diag_plan_for(g, prec).nblocks; }
+
+template <int P>
+static cudaError_t diag_launch_p(const void* state, double* partials, const Geom& g,
+                                 const HostColl& c, const DiagPlan& d, cudaStream_t st) {
+    constexpr size_t smem = diag_smem_bytes<P>();
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            diag_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    diag_kernel<P><<<d.nblocks, 32 * kDiagWarps, smem, st>>>(
+        (const typename Fmt<P>::S*)state, g.nx, g.ny, g.ps, c.inv_scale, d.nstrips, d.seglen,
+        d.nunits, partials);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
                         const Geom& g, const HostColl& c, cudaStream_t st) {
-    const DiagPlan d = diag_plan(g);
+    const DiagPlan d = diag_plan_for(g, prec);
     const int nb = d.nblocks;
-    LBMHD_DISPATCH(prec, (diag_kernel<P><<<nb, 32 * kDiagWarps, 0, st>>>(
-                             (const typename Fmt<P>::S*)state, g.nx, g.ny, g.ps, c.inv_scale,
-                             d.nstrips, d.seglen, d.nunits, partials)));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    LBMHD_DISPATCH(prec, (e = diag_launch_p<P>(state, partials, g, c, d, st)));
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, 256, 0, st>>>(partials, nb, (double)g.nx * g.ny, out12);
     return cudaGetLastError();

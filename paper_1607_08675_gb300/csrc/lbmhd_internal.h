@@ -83,7 +83,7 @@ cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Ge
                                 const HostColl& c, cudaStream_t st);
 
 // Diagnostics: per-block FP64 partials then one fixed-order final pass.
-int diag_num_blocks(const Geom& g);
+int diag_num_blocks(const Geom& g, int prec);
 cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
                         const Geom& g, const HostColl& c, cudaStream_t st);
 

@@ -87,7 +87,7 @@ extern "C" int lbmhd_diagnostics_noalloc(const void* state, int precision, int n
     g.nx = nx;
     g.ny = ny;
     g.ps = plane_stride;
-    if (diag_num_blocks(g) > kNoAllocRows) {
+    if (diag_num_blocks(g, precision) > kNoAllocRows) {
         set_error("diagnostics grid exceeds the 1024 partial rows of the static scratch");
         return LBMHD_EINVAL;
     }

@@ -215,7 +215,7 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out) {
         h->capturable = true;
     }
     const size_t bytes = (size_t)kNumPlanes * h->geom.ps * storage_bytes(p->precision);
-    const size_t pbytes = (size_t)diag_num_blocks(h->geom) * 12 * sizeof(double);
+    const size_t pbytes = (size_t)diag_num_blocks(h->geom, p->precision) * 12 * sizeof(double);
     void* mem[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     const size_t sizes[5] = {bytes, bytes, pbytes, 12 * sizeof(double), sizeof(int)};
     for (int i = 0; i < 5; ++i) {

@@ -177,6 +177,42 @@ def test_moments_and_diagnostics_match_oracle(L, orc):
     assert d["step"] == 60
 
 
+DIAG_TOL = {"fp64": 1e-11, "ff": 32 * 1e-11, "fp32": 1e-6, "fp32_dev": 1e-6, "fp16_dev": 1e-6}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff", "fp32", "fp16_dev"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (1, 2), (9, 1), (1, 9), (5, 3), (31, 7),
+                                   (61, 2), (30, 30), (30007, 53)])
+def test_diagnostics_ragged_shapes_match_oracle(L, orc, prec, shape):
+    """The diagnostics of the stored state against the oracle's of the same
+    state (decoded exactly): lattices narrower than one 30-column strip, one
+    node wide or high (both neighbours of a node are one node), strips with
+    a ragged last set of columns, and a 30007 x 53 lattice whose 1001
+    strips are cut into segments of several rows with a shorter last one
+    (53 is prime), so a warp's row ring wraps several times per segment.  Bars: the format's relative
+    bar on every quantity; the sums of rho u and B to that bar times the
+    mass (FP32 forms: 1e-9 of it); div B to the bar times the rms B."""
+    nx, ny = shape
+    kw = PRESETS["les_mrt"]
+    fields = inputs.orszag_tang(nx, ny, seed=6)
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision=prec, **kw))
+    L.lbmhd_init(h, *fields)
+    L.lbmhd_step(h, 20)
+    got = L.lbmhd_diagnostics(h)
+    ref = orc.diagnostics(L.lbmhd_get_state(h))
+    L.lbmhd_destroy(h)
+    tol = DIAG_TOL[prec]
+    floor = tol * (ref["E_kin"] + ref["E_mag"])
+    for k in ("mass", "E_kin", "E_mag", "enstrophy", "cross_helicity", "current_sq"):
+        assert abs(got[k] - ref[k]) <= tol * abs(ref[k]) + floor, (k, got[k], ref[k])
+    sums = 1e-9 if prec in ("fp32", "fp32_dev", "fp16_dev") else tol
+    for k in ("mom_x", "mom_y", "bsum_x", "bsum_y"):
+        assert abs(got[k] - ref[k]) <= sums * ref["mass"], (k, got[k], ref[k])
+    brms = np.sqrt(2.0 * ref["E_mag"])
+    for k in ("divB_max", "divB_rms"):
+        assert abs(got[k] - ref[k]) <= tol * brms, (k, got[k], ref[k])
+
+
 def test_diagnostics_deterministic(L):
     fields = inputs.turbulence(256, 256, seed=5)
     h = L.lbmhd_create(256, 256, L.lbmhd_params_default(precision="fp32"))
