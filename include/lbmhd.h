@@ -259,8 +259,10 @@ int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
  * (1024 rows of 12 doubles), held by every GPU that loads the library
  * until the process exits; every lattice the library accepts
  * (nx*ny <= 2^30) fits, larger ones are rejected with EINVAL.  The first
- * call on a device looks up the array's device address (once per device),
- * so make that first call before any stream capture.  All calls share the
+ * call on a device looks up the array's device address (once per device)
+ * and the first call for each precision queries the reduction kernel's
+ * occupancy (the work split follows it), so make those first calls before
+ * any stream capture.  All calls share the
  * array: calls that overlap on the GPU (other streams, other threads)
  * race and give wrong sums; serialise them.  Each call writes every
  * partial row it reads, so no clearing is needed between calls.
