@@ -1,5 +1,6 @@
 // lbmhd_aux.cu -- equilibrium initialisation, moments, state transfer,
 // the non-finite check and the FP64 diagnostics reduction.
+#include "lbmhd_cp_async.cuh"
 #include "lbmhd_device.cuh"
 #include "lbmhd_internal.h"
 
@@ -311,24 +312,6 @@ constexpr int kDiagRing = sizeof(typename Fmt<P>::S) == 2   ? 0
 template <int P>
 constexpr size_t diag_smem_bytes() {
     return (size_t)kDiagWarps * kDiagRing<P> * kPlanes * 32 * sizeof(typename Fmt<P>::S);
-}
-
-// One 4- or 8-byte cp.async (the L1-allocating form, the one that takes
-// sizes below 16 bytes), its commit and a wait for all but the N most
-// recent groups.
-template <int B>
-__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
-    static_assert(B == 4 || B == 8, "cp.async.ca copies 4, 8 or 16 bytes");
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 template <int P>
