@@ -293,29 +293,33 @@ inline DiagPlan diag_plan(const Geom& g, long long resident_warps, int nsm) {
 
 // Rows of stored values in flight per warp.  4- and 8-byte values are
 // staged by asynchronous copies (cp.async) into a per-warp ring of
-// kDiagRing<P> rows in shared memory: the next row is in flight while a row
-// is reduced without a register set to hold it, and the kernel keeps to 64
-// registers for the FP32 forms, four blocks per SM (the sweep is bound by
-// latency; with the next row prefetched into registers it ran at 107
-// registers, two blocks per SM).
-// Lane l copies and later reads back only its own column, so its own
-// wait_group is the only synchronisation the ring needs.  Two-byte FP16
-// values are read straight into registers, one row ahead only when that
-// pays (measured faster without: 0.94 ms vs 1.15 ms at 8192^2).
-#ifndef LBMHD_DIAG_RING4
-#define LBMHD_DIAG_RING4 3
-#endif
+// kDiagRing<P> rows in shared memory: the coming rows are in flight while a
+// row is reduced, with no register set to hold them (a prefetch of the
+// next row into registers took the kernel to 107 registers, two blocks per
+// SM).  Three rows for 4-byte values (depths 2 to 6 measured within 2% of
+// each other), two for 8-byte ones (the same bytes).  Lane l copies and
+// later reads back only its own column, so its own wait_group is the only
+// synchronisation the ring needs.  Two-byte FP16 values are read straight
+// into registers.
 template <int P>
 constexpr int kDiagRing = sizeof(typename Fmt<P>::S) == 2   ? 0
-                          : sizeof(typename Fmt<P>::S) == 4 ? LBMHD_DIAG_RING4
+                          : sizeof(typename Fmt<P>::S) == 4 ? 3
                                                             : 2;
 template <int P>
 constexpr size_t diag_smem_bytes() {
     return (size_t)kDiagWarps * kDiagRing<P> * kPlanes * 32 * sizeof(typename Fmt<P>::S);
 }
 
+// Blocks per SM the register budget is sized for.  FP16: three (80
+// registers; 0.78 ms at 8192^2, against 0.99 ms at 96 registers and 1.45
+// ms at the 64 ptxas picks with no minimum given).  FP32 forms: three as
+// well (80 registers; 117 at one block, no faster).  FP64 and FF: one (FF
+// loses 16% at three).
 template <int P>
-__global__ void __launch_bounds__(32 * kDiagWarps)
+constexpr int kDiagMinBlocks = (P == P_FP64 || P == P_FF) ? 1 : 3;
+
+template <int P>
+__global__ void __launch_bounds__(32 * kDiagWarps, kDiagMinBlocks<P>)
     diag_kernel(const typename Fmt<P>::S* __restrict__ st, int nx, int ny, long long ps,
                 float inv_scale, int nstrips, int seglen, long long nunits, double* partials) {
     using R = typename Fmt<P>::R;
