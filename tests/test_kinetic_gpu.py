@@ -190,12 +190,14 @@ def _run_variant(L, fields, steps, vec, **kw):
 @pytest.mark.parametrize("les", [2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev", "ff"])
 @pytest.mark.parametrize("shape", [(300, 41), (256, 7), (37, 23), (1, 9), (9, 1), (1, 1),
-                                   (2, 2), (513, 3)])
+                                   (2, 2), (513, 3), (4, 1), (4, 5), (8, 2), (516, 9),
+                                   (260, 1)])
 def test_fused_kernel_equals_two_pass_bitwise(L, prec, les, shape):
     """The default one-launch kernel (column strips swept in y, moment rows
     in a shared-memory ring) gives the two-pass kernels' bits: several
     strips with a ragged last one, one-row and one-column lattices, strips
-    narrower than the stencil, more row segments than rows."""
+    narrower than the stencil, more row segments than rows, a last strip
+    of 4 columns."""
     nx, ny = shape
     fields = inputs.orszag_tang(nx, ny, seed=6, amp=1e-3)
     kw = dict(KW, les=les, C_S=0.1 if les == 3 else 0.0, precision=prec)
