@@ -58,6 +58,37 @@ def test_noalloc_matches_handle_diagnostics_on_two_calls(L):
             assert _close(got[q], ref[key], key), (prec, key, got[q], ref[key])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev", "ff"])
+@pytest.mark.parametrize("pad", [0, 3])
+def test_noalloc_every_stored_format_bitwise(L, prec, pad):
+    """The raw stored state of every format, laid out with a plane stride of
+    nx*ny + pad elements (pad = 3 puts the plane starts off 16-byte
+    boundaries; the reduction's asynchronous copies need only element
+    alignment): the handle's own diagnostics bit for bit -- the same kernel
+    and work split over the same values."""
+    import torch
+
+    nx, ny = 123, 77
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision=prec))
+    L.lbmhd_init(h, *inputs.turbulence(nx, ny, kmin=2, kmax=5, seed=7))
+    L.lbmhd_step(h, 30)
+    ref = L.lbmhd_diagnostics(h)
+    raw = L.lbmhd_get_state_raw(h)
+    L.lbmhd_destroy(h)
+    if raw.dtype == np.uint16:
+        raw = raw.view(np.int16)
+    tail = raw.shape[3:]
+    ps = nx * ny + pad
+    buf = np.zeros((19, ps) + tail, dtype=raw.dtype)
+    buf[:, : nx * ny] = raw.reshape((19, nx * ny) + tail)
+    state = torch.from_numpy(buf).cuda()
+    out = torch.full((12,), float("nan"), dtype=torch.float64, device="cuda")
+    L.lbmhd_diagnostics_noalloc(state, prec, nx, ny, ps, out)
+    got = out.cpu().numpy()
+    for q, key in enumerate(L.DIAG_KEYS):
+        assert got[q] == ref[key], (prec, pad, key, got[q], ref[key])
+
+
 def test_noalloc_rejects_oversized_and_bad_arguments(L):
     import torch
 
