@@ -297,17 +297,24 @@ inline DiagPlan diag_plan(const Geom& g, long long resident_warps, int nsm) {
 // row is reduced, with no register set to hold them (a prefetch of the
 // next row into registers took the kernel to 107 registers, two blocks per
 // SM).  Three rows for 4-byte values (depths 2 to 6 measured within 2% of
-// each other), two for 8-byte ones (the same bytes).  Lane l copies and
-// later reads back only its own column, so its own wait_group is the only
-// synchronisation the ring needs.  Two-byte FP16 values are read straight
-// into registers.
+// each other), two for 8-byte ones (the same bytes).  In the per-lane form
+// lane l copies and later reads back only its own column, so its own
+// wait_group is the only synchronisation the ring needs; the wide form (in
+// the kernel) copies 16-byte granules and adds warp barriers.  Two-byte
+// FP16 values are read straight into registers.
 template <int P>
 constexpr int kDiagRing = sizeof(typename Fmt<P>::S) == 2   ? 0
                           : sizeof(typename Fmt<P>::S) == 4 ? 3
                                                             : 2;
-template <int P>
+// Elements of one staged plane row: 32 (one per lane), or in the wide form
+// (4-byte values) the 36 of a 16-byte aligned window over the warp's 32
+// columns.
+template <int P, bool WIDE>
+constexpr int kDiagRowE = WIDE ? 36 : 32;
+template <int P, bool WIDE>
 constexpr size_t diag_smem_bytes() {
-    return (size_t)kDiagWarps * kDiagRing<P> * kPlanes * 32 * sizeof(typename Fmt<P>::S);
+    return (size_t)kDiagWarps * kDiagRing<P> * kPlanes * kDiagRowE<P, WIDE> *
+           sizeof(typename Fmt<P>::S);
 }
 
 // Blocks per SM the register budget is sized for.  FP16: three (80
@@ -318,7 +325,7 @@ constexpr size_t diag_smem_bytes() {
 template <int P>
 constexpr int kDiagMinBlocks = (P == P_FP64 || P == P_FF) ? 1 : 3;
 
-template <int P>
+template <int P, bool WIDE>
 __global__ void __launch_bounds__(32 * kDiagWarps, kDiagMinBlocks<P>)
     diag_kernel(const typename Fmt<P>::S* __restrict__ st, int nx, int ny, long long ps,
                 float inv_scale, int nstrips, int seglen, long long nunits, double* partials) {
@@ -327,10 +334,13 @@ __global__ void __launch_bounds__(32 * kDiagWarps, kDiagMinBlocks<P>)
     using S = typename Fmt<P>::S;
     constexpr int K = kDiagRing<P>;
     static_assert(K == 0 || K >= 2, "the ring holds rows y - 1 and y while y + 1 lands");
+    static_assert(!WIDE || (K > 0 && sizeof(S) == 4), "wide rows: 4-byte values in the ring");
     extern __shared__ __align__(16) unsigned char diag_ring_smem[];
     __shared__ double red[kDiagWarps][kNQ];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    S* ring = reinterpret_cast<S*>(diag_ring_smem) + (size_t)warp * K * kPlanes * 32 + lane;
+    constexpr int RE = kDiagRowE<P, WIDE>;
+    S* ring0 = reinterpret_cast<S*>(diag_ring_smem) + (size_t)warp * K * kPlanes * RE;
+    S* ring = ring0 + lane;
     A acc[kNQ];
 #pragma unroll
     for (int q = 0; q < kNQ; ++q) acc[q] = A(0);
@@ -444,30 +454,77 @@ __global__ void __launch_bounds__(32 * kDiagWarps, kDiagMinBlocks<P>)
             // past the last row, keeps "row t done" = "at most K - 1 groups
             // pending".
             const int nrows = y1 - y0 + 2;
-            auto issue = [&](int t) {
-                if (t < nrows) {
-                    const S* src = fetch_ptr();
-                    S* dst = ring + (t % K) * (kPlanes * 32);
-#pragma unroll
-                    for (int i = 0; i < kPlanes; ++i)
-                        cp_async_small<sizeof(S)>(dst + i * 32, src + i * ps);
-                }
-                cp_async_commit();
-            };
             int tn = 0;  // the next row to take
-            auto take = [&](R (&m)[kNM]) {
-                cp_async_wait<K - 1>();
-                S raw[kPlanes];
-                const S* p = ring + (tn % K) * (kPlanes * 32);
+            // Wide form (4-byte values, rows and planes 16-byte aligned, nx a
+            // multiple of 4): plane i's columns [wx, wx + 36), wx = (x0 - 1)
+            // rounded down to a multiple of 4, arrive as 9 copies of 16
+            // bytes, each granule from its column modulo nx (the periodic
+            // wrap at the row ends; nx is a multiple of 4, so a granule
+            // never straddles it).  Lane l < 27 copies granule l % 9 of
+            // planes l / 9, l / 9 + 3, ... (7 instructions per row instead
+            // of 19), so lanes read one another's copies: a warp barrier
+            // after the wait, and another before a slot is refilled.
+            if constexpr (WIDE) {
+                const int wx = (x0 - 1) & ~3;  // floor to a multiple of 4 (x0 - 1 >= -1)
+                const int off = (x0 - 1) - wx + (lane <= sw + 1 ? lane : 1);
+                const int grp = lane / 9, part = lane - 9 * (lane / 9);
+                int gcol = (wx + 4 * part) % nx;  // this lane's granule, wrapped
+                if (gcol < 0) gcol += nx;
+                const long long ps3 = 3 * ps;
+                auto issue_w = [&](int t) {
+                    if (t < nrows) {
+                        const S* src = fetch_ptr() - col + gcol + grp * ps;
+                        S* dst = ring0 + (t % K) * (kPlanes * RE) + grp * RE + 4 * part;
+                        if (lane < 27) {
 #pragma unroll
-                for (int i = 0; i < kPlanes; ++i) raw[i] = p[i * 32];
-                node_moments_raw<P>(raw, inv_scale, m);
-                issue(tn + K);  // the slot is free once its values are in registers
-                ++tn;
-            };
+                            for (int j = 0; j < 7; ++j) {
+                                if (grp + 3 * j < kPlanes) cp_async_16(dst + 3 * j * RE, src);
+                                src += ps3;
+                            }
+                        }
+                    }
+                    cp_async_commit();
+                };
+                auto take_w = [&](R (&m)[kNM]) {
+                    cp_async_wait<K - 1>();
+                    __syncwarp();
+                    S raw[kPlanes];
+                    const S* p = ring0 + (tn % K) * (kPlanes * RE) + off;
 #pragma unroll
-            for (int t = 0; t < K; ++t) issue(t);
-            sweep(take);
+                    for (int i = 0; i < kPlanes; ++i) raw[i] = p[i * RE];
+                    node_moments_raw<P>(raw, inv_scale, m);
+                    __syncwarp();
+                    issue_w(tn + K);
+                    ++tn;
+                };
+#pragma unroll
+                for (int t = 0; t < K; ++t) issue_w(t);
+                sweep(take_w);
+            } else {
+                auto issue = [&](int t) {
+                    if (t < nrows) {
+                        const S* src = fetch_ptr();
+                        S* dst = ring + (t % K) * (kPlanes * RE);
+#pragma unroll
+                        for (int i = 0; i < kPlanes; ++i)
+                            cp_async_small<sizeof(S)>(dst + i * RE, src + i * ps);
+                    }
+                    cp_async_commit();
+                };
+                auto take = [&](R (&m)[kNM]) {
+                    cp_async_wait<K - 1>();
+                    S raw[kPlanes];
+                    const S* p = ring + (tn % K) * (kPlanes * RE);
+#pragma unroll
+                    for (int i = 0; i < kPlanes; ++i) raw[i] = p[i * RE];
+                    node_moments_raw<P>(raw, inv_scale, m);
+                    issue(tn + K);  // the slot is free once its values are in registers
+                    ++tn;
+                };
+#pragma unroll
+                for (int t = 0; t < K; ++t) issue(t);
+                sweep(take);
+            }
             cp_async_wait<0>();
         } else {
             auto load = [&](R (&m)[kNM]) {
@@ -595,23 +652,25 @@ cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Ge
     return cudaGetLastError();
 }
 
-// Warps of diag_kernel<P> resident on the device at once (the kernel's
-// registers and ring bound its blocks per SM), found once per process.
+// Warps of diag_kernel<P, WIDE> resident on the device at once (the
+// kernel's registers and ring bound its blocks per SM), found once per
+// process.
 struct DiagOcc {
     long long warps;  // resident warps of the kernel on the device
     int nsm;
 };
-template <int P>
+template <int P, bool WIDE>
 static DiagOcc diag_occupancy() {
     static const DiagOcc o = [] {
-        constexpr size_t smem = diag_smem_bytes<P>();
+        constexpr size_t smem = diag_smem_bytes<P, WIDE>();
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(diag_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+            cudaFuncSetAttribute(diag_kernel<P, WIDE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0, nsm = 0, bps = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, diag_kernel<P>, 32 * kDiagWarps, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, diag_kernel<P, WIDE>,
+                                                      32 * kDiagWarps, smem);
         cudaGetLastError();  // a failed query leaves the floors below
         nsm = nsm > 0 ? nsm : 1;
         return DiagOcc{(long long)nsm * (bps > 0 ? bps : 1) * kDiagWarps, nsm};
@@ -619,31 +678,48 @@ static DiagOcc diag_occupancy() {
     return o;
 }
 
-static DiagPlan diag_plan_for(const Geom& g, int prec) {
+// The wide form serves 4-byte storage whose rows and planes start on
+// 16-byte boundaries.
+static bool diag_wide(int prec, const Geom& g, const void* state) {
+    return (prec == P_FP32 || prec == P_FP32_DEV) && g.nx % 4 == 0 && g.ps % 4 == 0 &&
+           ((uintptr_t)state & 15) == 0;
+}
+
+static DiagPlan diag_plan_for(const Geom& g, int prec, bool wide) {
     DiagOcc o{kDiagWarps, 1};
     switch (prec) {
-        case P_FP64: o = diag_occupancy<P_FP64>(); break;
-        case P_FP32: o = diag_occupancy<P_FP32>(); break;
-        case P_FP32_DEV: o = diag_occupancy<P_FP32_DEV>(); break;
-        case P_FP16_DEV: o = diag_occupancy<P_FP16_DEV>(); break;
-        case P_FF: o = diag_occupancy<P_FF>(); break;
+        case P_FP64: o = diag_occupancy<P_FP64, false>(); break;
+        case P_FP32:
+            o = wide ? diag_occupancy<P_FP32, true>() : diag_occupancy<P_FP32, false>();
+            break;
+        case P_FP32_DEV:
+            o = wide ? diag_occupancy<P_FP32_DEV, true>() : diag_occupancy<P_FP32_DEV, false>();
+            break;
+        case P_FP16_DEV: o = diag_occupancy<P_FP16_DEV, false>(); break;
+        case P_FF: o = diag_occupancy<P_FF, false>(); break;
         default: break;
     }
     return diag_plan(g, o.warps, o.nsm);
 }
 
-int diag_num_blocks(const Geom& g, int prec) { return diag_plan_for(g, prec).nblocks; }
+// Partial rows a reduction of this lattice may need (either form).
+int diag_num_blocks(const Geom& g, int prec) {
+    const int a = diag_plan_for(g, prec, false).nblocks;
+    const bool w = prec == P_FP32 || prec == P_FP32_DEV;
+    const int b = w ? diag_plan_for(g, prec, true).nblocks : a;
+    return a > b ? a : b;
+}
 
-template <int P>
+template <int P, bool WIDE>
 static cudaError_t diag_launch_p(const void* state, double* partials, const Geom& g,
                                  const HostColl& c, const DiagPlan& d, cudaStream_t st) {
-    constexpr size_t smem = diag_smem_bytes<P>();
+    constexpr size_t smem = diag_smem_bytes<P, WIDE>();
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(
-            diag_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            diag_kernel<P, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    diag_kernel<P><<<d.nblocks, 32 * kDiagWarps, smem, st>>>(
+    diag_kernel<P, WIDE><<<d.nblocks, 32 * kDiagWarps, smem, st>>>(
         (const typename Fmt<P>::S*)state, g.nx, g.ny, g.ps, c.inv_scale, d.nstrips, d.seglen,
         d.nunits, partials);
     return cudaGetLastError();
@@ -651,10 +727,16 @@ static cudaError_t diag_launch_p(const void* state, double* partials, const Geom
 
 cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
                         const Geom& g, const HostColl& c, cudaStream_t st) {
-    const DiagPlan d = diag_plan_for(g, prec);
+    const bool wide = diag_wide(prec, g, state);
+    const DiagPlan d = diag_plan_for(g, prec, wide);
     const int nb = d.nblocks;
     cudaError_t e = cudaSuccess;
-    LBMHD_DISPATCH(prec, (e = diag_launch_p<P>(state, partials, g, c, d, st)));
+    if (wide && prec == P_FP32)
+        e = diag_launch_p<P_FP32, true>(state, partials, g, c, d, st);
+    else if (wide)
+        e = diag_launch_p<P_FP32_DEV, true>(state, partials, g, c, d, st);
+    else
+        LBMHD_DISPATCH(prec, (e = diag_launch_p<P, false>(state, partials, g, c, d, st)));
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, 256, 0, st>>>(partials, nb, (double)g.nx * g.ny, out12);
     return cudaGetLastError();
