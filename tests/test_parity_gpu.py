@@ -182,14 +182,17 @@ DIAG_TOL = {"fp64": 1e-11, "ff": 32 * 1e-11, "fp32": 1e-6, "fp32_dev": 1e-6, "fp
 
 @pytest.mark.parametrize("prec", ["fp64", "ff", "fp32", "fp16_dev"])
 @pytest.mark.parametrize("shape", [(1, 1), (2, 1), (1, 2), (9, 1), (1, 9), (5, 3), (31, 7),
-                                   (61, 2), (30, 30), (30007, 53)])
+                                   (61, 2), (30, 30), (30007, 53), (4, 5), (8, 3), (248, 9)])
 def test_diagnostics_ragged_shapes_match_oracle(L, orc, prec, shape):
     """The diagnostics of the stored state against the oracle's of the same
     state (decoded exactly): lattices narrower than one 30-column strip, one
     node wide or high (both neighbours of a node are one node), strips with
     a ragged last set of columns, and a 30007 x 53 lattice whose 1001
     strips are cut into segments of several rows with a shorter last one
-    (53 is prime), so a warp's row ring wraps several times per segment.  Bars: the format's relative
+    (53 is prime), so a warp's row ring wraps several times per segment;
+    and 16-byte aligned rows (nx = 4, 8, 248), where the FP32 and FP16 forms
+    copy aligned windows whose granules wrap around short rows more than
+    once, with a ragged last strip at 248.  Bars: the format's relative
     bar on every quantity; the sums of rho u and B to that bar times the
     mass (FP32 forms: 1e-9 of it); div B to the bar times the rms B."""
     nx, ny = shape

@@ -60,15 +60,18 @@ def test_noalloc_matches_handle_diagnostics_on_two_calls(L):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_dev", "fp16_dev", "ff"])
 @pytest.mark.parametrize("pad", [0, 3])
-def test_noalloc_every_stored_format_bitwise(L, prec, pad):
+@pytest.mark.parametrize("shape", [(123, 77), (128, 77)])
+def test_noalloc_every_stored_format_bitwise(L, prec, pad, shape):
     """The raw stored state of every format, laid out with a plane stride of
-    nx*ny + pad elements (pad = 3 puts the plane starts off 16-byte
-    boundaries; the reduction's asynchronous copies need only element
-    alignment): the handle's own diagnostics bit for bit -- the same kernel
-    and work split over the same values."""
+    nx*ny + pad elements: the handle's own diagnostics bit for bit -- the
+    same work split and arithmetic over the same values.  With nx = 128 the
+    handle and the unpadded layout take the reduction's wide form (16-byte
+    copies of aligned row windows, FP32 and FP16), the padded one (plane
+    starts off 16-byte boundaries) its per-lane copies; nx = 123 takes the
+    per-lane form throughout."""
     import torch
 
-    nx, ny = 123, 77
+    nx, ny = shape
     h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision=prec))
     L.lbmhd_init(h, *inputs.turbulence(nx, ny, kmin=2, kmax=5, seed=7))
     L.lbmhd_step(h, 30)
