@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -297,16 +298,23 @@ def run_batched(L, args, stream, rank, hbm, barrier, max_over_ranks):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     mlups = world * cells * steps / t_batch / 1e6
     # the same ensemble with the paper's kinetic LES (les = 2, Delta = 2):
-    # a moments pass and the step over all runs per step, against the runs
-    # one after another with their own (fused) single-lattice kernel
-    ksteps = max(2, steps // 4)
+    # the fused kernel over every run's strip-segments, one launch per step
+    # (152 B/node), against the runs one after another with their own
+    # single-lattice launches of the same kernel; at least MIN_LEG_S of
+    # device time
     kw = dict(TURB_RATES, les=2, delta=2.0)
     kb = L.lbmhd_batch_create(nx, ny, tau, tau, cs,
                               L.lbmhd_params_default(precision="fp32", stream=stream, **kw))
+    kshape = L.lbmhd_batch_get_launch(kb)
     for i, r in enumerate(runs):
         L.lbmhd_batch_init(kb, i, *inputs.turbulence(r["nx"], r["ny"], seed=r["seed"]))
     L.lbmhd_batch_step(kb, 8)
     barrier()
+    e0.record(stream)
+    L.lbmhd_batch_step(kb, 4)
+    e1.record(stream)
+    e1.synchronize()
+    ksteps = steps_for(e0.elapsed_time(e1) / 1e3 / 4)
     e0.record(stream)
     L.lbmhd_batch_step(kb, ksteps)
     e1.record(stream)
@@ -331,9 +339,12 @@ def run_batched(L, args, stream, rank, hbm, barrier, max_over_ranks):
     tk_seq = max_over_ranks(tk_seq)
     kinetic = {"MLUPS": world * cells * ksteps / tk_batch / 1e6,
                "sequential_MLUPS": world * cells * ksteps / tk_seq / 1e6,
-               "speedup": tk_seq / tk_batch, "steps": ksteps,
-               "note": "les=2 ensemble (moments pass + step per step, 268 B/node) vs the runs "
-                       "one by one with the fused single-lattice kernel (152 B/node)"}
+               "speedup": tk_seq / tk_batch, "steps": ksteps, "seconds": tk_batch,
+               "hbm_frac": cells * ksteps * 152 / tk_batch / 1e9 / hbm,
+               "kernel": "fused" if kshape[0] == 1 else "two-pass",
+               "note": "les=2 ensemble: the fused kernel over every run's strip-segments, one "
+                       "launch per step (152 B/node), vs the runs one by one with the fused "
+                       "single-lattice kernel"}
     return {"MLUPS": mlups, "sequential_MLUPS": world * cells * steps / t_seq / 1e6,
             "kinetic_les": kinetic,
             "speedup": t_seq / t_batch, "runs": len(runs), "cells": cells, "steps": steps,
@@ -509,6 +520,24 @@ def timed_steps(L, h, stream, steps, warmup):
     return e0.elapsed_time(e1) / 1e3
 
 
+# Every secondary leg times at least this much device time, whatever --steps
+# is, so that its figure does not hang on a handful of launches.
+MIN_LEG_S = 0.1
+
+
+def steps_for(seconds_per_step, min_s=MIN_LEG_S, floor=2):
+    """Steps that fill min_s of device time at the probed rate."""
+    return max(floor, int(math.ceil(min_s / max(seconds_per_step, 1e-9))))
+
+
+def timed_leg(L, h, stream, warmup, max_over_ranks_):
+    """(steps, seconds) of a leg timed for at least MIN_LEG_S: a 2-step probe
+    after the warm-up sets the step count; max over ranks."""
+    probe = timed_steps(L, h, stream, 2, warmup) / 2
+    steps = steps_for(probe)
+    return steps, max_over_ranks_(timed_steps(L, h, stream, steps, 1))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -576,35 +605,35 @@ def run_ours(args):
         # the paper's kinetic LES, FP32: the fused one-launch kernel (default;
         # algorithmic bytes per node 19 reads + 19 writes, as a plain step) and
         # the two-pass kernels (19 reads + 5 writes, 19 + 5 reads + 19 writes)
-        for kname, kvec, kbytes in (("fp32_kinetic_les", 1, 152),
-                                    ("fp32_kinetic_les_two_pass", 0, 268)):
+        # and the cross-helicity closure (les = 3) with the fused kernel
+        for kname, kles, kvec, kbytes in (("fp32_kinetic_les", 2, 1, 152),
+                                          ("fp32_kinetic_les_two_pass", 2, 0, 268),
+                                          ("fp32_cross_helicity", 3, 1, 152)):
             hk = L.lbmhd_create(n, n, L.lbmhd_params_default(
-                precision="fp32", **dict(kw, les=2, delta=2.0)))
+                precision="fp32", **dict(kw, les=kles, delta=2.0)))
             L.lbmhd_set_launch(hk, kvec, 256)
             L.lbmhd_init(hk, *fields)
             barrier()
-            ksteps = max(2, args.steps // 5)
-            t = max_over_ranks_(timed_steps(L, hk, stream, ksteps, max(3, args.warmup // 10)))
+            ksteps, t = timed_leg(L, hk, stream, max(3, args.warmup // 10), max_over_ranks_)
             L.lbmhd_destroy(hk)
+            what = ("les=2 (filtered equilibria, Delta=2), " if kles == 2 else
+                    "les=3 (cross-helicity closure, Delta=2), ")
             variants[kname] = {
-                "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps,
+                "MLUPS": world * cells * ksteps / t / 1e6, "steps": ksteps, "seconds": t,
                 "bytes_per_cell": kbytes,
                 "hbm_frac": kbytes * cells * ksteps / t / 1e9 / hbm,
-                "note": "les=2 (filtered equilibria, Delta=2), " + (
-                    "fused: one launch per step" if kvec else "moments pass + step")}
-        for vp, vsteps in (("fp64", args.steps // 10), ("ff", args.steps // 4),
-                           ("fp32_dev", args.steps), ("fp16_dev", args.steps)):
+                "note": what + ("fused: one launch per step" if kvec else "moments pass + step")}
+        for vp in ("fp64", "ff", "fp32_dev", "fp16_dev"):
             if vp == prec:
                 continue
-            vsteps = max(2, vsteps)
             hv = L.lbmhd_create(n, n, L.lbmhd_params_default(precision=vp, **kw))
             L.lbmhd_init(hv, *fields)
             barrier()
-            t = max_over_ranks_(timed_steps(L, hv, stream, vsteps, max(3, args.warmup // 10)))
+            vsteps, t = timed_leg(L, hv, stream, max(3, args.warmup // 10), max_over_ranks_)
             L.lbmhd_destroy(hv)
             vb = L.lbmhd_bytes_per_cell(vp)
             variants[vp] = {
-                "MLUPS": world * cells * vsteps / t / 1e6, "steps": vsteps,
+                "MLUPS": world * cells * vsteps / t / 1e6, "steps": vsteps, "seconds": t,
                 "bytes_per_cell": vb,
                 "hbm_frac": vb * cells * vsteps / t / 1e9 / hbm,
             }
@@ -619,17 +648,22 @@ def run_ours(args):
         L.lbmhd_step(hd, 2)
         L.lbmhd_diagnostics(hd)
         barrier()
-        reps = 10
         d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        for _ in range(reps):
-            L.lbmhd_diagnostics(hd)
-        d1.record(stream)
-        d1.synchronize()
-        t = max_over_ranks_(d0.elapsed_time(d1) / 1e3 / reps)
+        reps = 2
+        for attempt in range(2):  # a probe, then enough calls for MIN_LEG_S
+            d0.record(stream)
+            for _ in range(reps):
+                L.lbmhd_diagnostics(hd)
+            d1.record(stream)
+            d1.synchronize()
+            t = d0.elapsed_time(d1) / 1e3 / reps
+            if attempt == 0:
+                reps = steps_for(t)
+        t = max_over_ranks_(t)
         L.lbmhd_destroy(hd)
         dbytes = L.lbmhd_bytes_per_cell(prec) // 2
-        diagnostics = {"ms": 1e3 * t, "bytes_per_cell": dbytes,
+        diagnostics = {"ms": 1e3 * t, "calls": reps, "seconds": t * reps,
+                       "bytes_per_cell": dbytes,
                        "GBps": dbytes * cells / t / 1e9, "hbm_frac": dbytes * cells / t / 1e9 / hbm,
                        "note": "lbmhd_diagnostics (12 FP64 sums, div B, |j|^2) of the "
                                f"{prec} state, per call"}

@@ -221,12 +221,22 @@ const void* pick_kernel(int prec, int vec) {
     return nullptr;
 }
 
+// Rows per segment of the fused kinetic ensemble kernel: segments of at
+// most 128 rows, of even length within a run (each segment forms two moment
+// rows again, 1.6% extra pulls at 128).
+int kin_seglen(int ny) {
+    const int nseg = (ny + 127) / 128;
+    return (ny + nseg - 1) / nseg;
+}
+
 template <class R>
 int upload_runs_t(lbmhd_batch_t* b) {
     std::vector<RunDev<R>> rd(b->nruns);
     std::vector<int> map;
     unsigned unit = 0;
     long long moff = 0;
+    const bool kin = b->p.les >= 2;
+    const int ksw = kinetic_fused_strip(b->p.precision);
     for (int r = 0; r < b->nruns; ++r) {
         const HostColl hc = run_coll(b, r);
         rd[r].off = b->off[r];
@@ -235,10 +245,17 @@ int upload_runs_t(lbmhd_batch_t* b) {
         rd[r].ps = b->ps[r];
         rd[r].nx = b->nx[r];
         rd[r].ny = b->ny[r];
-        rd[r].total = (unsigned)((long long)b->nx[r] / b->vec * b->ny[r]);
+        // kinetic closures: one node per thread (vec 0 selects the two-pass kernels)
+        const int v = kin ? 1 : b->vec;
+        rd[r].total = (unsigned)((long long)b->nx[r] / v * b->ny[r]);
         rd[r].unit0 = unit;
+        rd[r].kstrips = (b->nx[r] + ksw - 1) / ksw;
+        rd[r].kseglen = kin_seglen(b->ny[r]);
         rd[r].c = coll_for_prec<R>(hc, b->p.precision);
-        const unsigned units = (rd[r].total + b->block - 1) / b->block;
+        const unsigned units =
+            kin && b->vec == 1
+                ? (unsigned)rd[r].kstrips * (unsigned)((b->ny[r] + rd[r].kseglen - 1) / rd[r].kseglen)
+                : (rd[r].total + b->block - 1) / b->block;
         for (unsigned u = 0; u < units; ++u) map.push_back(r);
         unit += units;
     }
@@ -262,6 +279,12 @@ int configure(lbmhd_batch_t* b) {
              : b->p.precision == LBMHD_FF ? upload_runs_t<ff>(b)
                                           : upload_runs_t<float>(b);
     if (rc) return rc;
+    if (b->p.les >= 2) {  // one CTA per unit, no persistent grid
+        b->grid = 1;
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        return LBMHD_OK;
+    }
     const void* k = pick_kernel(b->p.precision, b->vec);
     if (!k) return bfail(LBMHD_EINVAL, "no batched kernel for this precision / vector width");
     int per_sm = 0, sms = 0;
@@ -277,13 +300,13 @@ int configure(lbmhd_batch_t* b) {
 }
 
 cudaError_t launch_batch(lbmhd_batch_t* b, int nsteps, int parity) {
-    if (b->p.les >= 2) {  // kinetic closures: moments pass + step per step
+    if (b->p.les >= 2) {  // kinetic closures: the fused kernel, or moments pass + step
         const HostColl hc = run_coll(b, 0);
         for (int s = 0; s < nsteps; ++s) {
             const bool odd = ((parity + s) & 1) != 0;
             const cudaError_t e = launch_batch_kinetic(
-                b->p.precision, hc.kin, b->d_runs, b->d_unit_run, b->nunits, b->block,
-                odd ? b->buf[1] : b->buf[0], odd ? b->buf[0] : b->buf[1], b->d_mom,
+                b->p.precision, hc.kin, b->vec == 1, b->d_runs, b->d_unit_run, b->nunits,
+                b->block, odd ? b->buf[1] : b->buf[0], odd ? b->buf[0] : b->buf[1], b->d_mom,
                 hc.inv_scale, b->stream);
             if (e != cudaSuccess) return e;
         }
@@ -540,8 +563,14 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
     b->vec = v;
     b->block = v == 4 ? 64 : 128;
     b->spl = 8;
-    if (common->les >= 2) {  // kinetic closures: one node per thread, one step per launch
-        b->vec = 1;
+    if (common->les >= 2) {
+        // kinetic closures, one step per launch: the fused kernel (vec 1)
+        // where the single lattice takes it, else the two-pass kernels (vec 0,
+        // 128 nodes per unit) -- FP64, and FF with the filtered equilibria
+        b->vec = common->precision == LBMHD_FP64 ||
+                         (common->precision == LBMHD_FF && common->les == 2)
+                     ? 0
+                     : 1;
         b->block = 128;
         b->spl = 1;
     }
@@ -557,15 +586,20 @@ int lbmhd_batch_create(int nruns, const int* nx, const int* ny, const double* ta
 int lbmhd_batch_set_launch(lbmhd_batch_t* b, int vec, int block, int steps_per_launch) {
     int rc = check_batch(b);
     if (rc) return rc;
-    if (vec != 1 && vec != 2 && vec != 4) return bfail(LBMHD_EINVAL, "vec must be 1, 2 or 4");
-    for (int r = 0; r < b->nruns; ++r)
-        if (b->nx[r] % vec) return bfail(LBMHD_EINVAL, "vec must divide every run's nx");
+    if (b->p.les >= 2) {
+        if ((vec != 0 && vec != 1) || steps_per_launch != 1)
+            return bfail(LBMHD_EINVAL,
+                         "les 2, 3 ensembles: vec 1 (fused kernel) or 0 (two-pass kernels), "
+                         "one step per launch");
+    } else {
+        if (vec != 1 && vec != 2 && vec != 4) return bfail(LBMHD_EINVAL, "vec must be 1, 2 or 4");
+        for (int r = 0; r < b->nruns; ++r)
+            if (b->nx[r] % vec) return bfail(LBMHD_EINVAL, "vec must divide every run's nx");
+    }
     if (block < 32 || block > 256 || block % 32)
         return bfail(LBMHD_EINVAL, "block must be a multiple of 32 in [32, 256]");
     if (steps_per_launch < 1 || steps_per_launch > 4096)
         return bfail(LBMHD_EINVAL, "steps_per_launch must be in [1, 4096]");
-    if (b->p.les >= 2 && (vec != 1 || steps_per_launch != 1))
-        return bfail(LBMHD_EINVAL, "les 2, 3 ensembles: vec 1 and one step per launch");
     LBMHD_BCK(b, cudaStreamSynchronize(b->stream));
     b->vec = vec;
     b->block = block;
@@ -749,7 +783,7 @@ int lbmhd_batch_autotune(lbmhd_batch_t* b, const char* cache_path, int trial_ste
     LBMHD_BCK(b, cudaEventCreate(&e1));
     double best = -1.0;
     int bv = b->vec, bb = b->block, bs = b->spl;
-    const int vecs[3] = {4, 2, 1};
+    const int vecs[4] = {4, 2, 1, 0};
     const int blocks[3] = {64, 128, 256};
     const int spls[3] = {1, 8, 64};
     for (int v : vecs)

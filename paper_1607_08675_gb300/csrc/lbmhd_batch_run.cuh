@@ -14,6 +14,8 @@ struct RunDev {
     int nx, ny;
     unsigned total;  // live threads of the run (nx / V * ny)
     unsigned unit0;  // first work unit of the run
+    int kstrips;     // fused kinetic kernel: column strips of the run
+    int kseglen;     // ... and rows per segment (units = strips x segments)
     Coll<R> c;
 };
 

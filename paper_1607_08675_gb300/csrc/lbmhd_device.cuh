@@ -306,4 +306,134 @@ __device__ __forceinline__ void collide(R (&d)[9], R (&g)[10], const Coll<R>& c,
     for (int q = 0; q < 10; ++q) g[q] -= sm * (g[q] - geq[q]);
 }
 
+// Fused multiply-add in the arithmetic type: one rounding for FP32 and FP64,
+// the double-word product and sum for FF.  kfma(k, x, y) = k x + y for a
+// small constant k (kmul's exact or cheap scaling for FF).
+template <class R>
+__device__ __forceinline__ R fmad(R a, R b, R c) {
+    return a * b + c;
+}
+template <>
+__device__ __forceinline__ float fmad(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+}
+template <>
+__device__ __forceinline__ double fmad(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+}
+template <class R>
+__device__ __forceinline__ R kfma(float k, R x, R y) {
+    return kmul(k, x) + y;
+}
+template <>
+__device__ __forceinline__ float kfma(float k, float x, float y) {
+    return __fmaf_rn(k, x, y);
+}
+template <>
+__device__ __forceinline__ double kfma(float k, double x, double y) {
+    return __fma_rn((double)k, x, y);
+}
+
+// The collision of collide() with its products and sums written as explicit
+// fused multiply-adds (fmad, kfma), for kernels compiled without contraction
+// (the kinetic closures' file): there the compiler fuses nothing by itself,
+// so kernels of different shape that call this function round every
+// operation the same way and give the same bits, and the explicit fusions
+// save the instructions contraction would.  Same moments, equilibria,
+// rates and relaxation as collide(), same template flags.
+template <class R, bool SCALED = false, bool KIN = false, bool TAUS = false>
+__device__ __forceinline__ void collide_xf(R (&d)[9], R (&g)[10], const Coll<R>& c,
+                                           const R* sh = nullptr) {
+    constexpr R k1_3 = R(1) / R(3), k1_6 = R(1) / R(6), k5_3 = R(5) / R(3);
+    constexpr R k1_12 = R(1) / R(12), k1_20 = R(1) / R(20), k1_180 = R(1) / R(180);
+    const R dsum9 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R rho = SCALED ? fmad(dsum9, c.inv_s, R(1)) : R(1) + dsum9;
+    const R irho = rcp(rho);
+    const R ux = jx * irho, uy = jy * irho;
+    const R bx = (g[0] + g[2]) + (g[4] + g[6]) + g[8];
+    const R by = (g[1] + g[3]) + (g[5] + g[7]) + g[9];
+
+    const R dsum = (d[5] + d[6]) + (d[7] + d[8]);
+    const R s1234 = (d[1] + d[2]) + (d[3] + d[4]);
+    const R m3 = (d[5] - d[6]) + (d[7] - d[8]);
+    const R m4 = (d[1] + d[3]) - (d[2] + d[4]);
+    const R m5 = kfma(2, d[3] - d[1], (d[5] - d[6]) + (d[8] - d[7]));
+    const R m6 = kfma(2, d[4] - d[2], (d[5] + d[6]) - (d[7] + d[8]));
+    const R m7 = kfma(-5, s1234, kmul(4, d[0] + dsum));
+    const R m8 = kfma(4, d[0], -dsum);
+
+    R j2i = fmad(jx, jx, jy * jy) * irho;
+    R q3 = fmad(jx * jy, irho, -(bx * by));
+    R q4 = fmad(fmad(jx, jx, -(jy * jy)), irho, fmad(by, by, -(bx * bx)));
+    R E = fmad(ux, by, -(uy * bx));
+    if (SCALED) {
+        j2i *= c.inv_s;
+        q3 *= c.inv_s;
+        q4 *= c.inv_s;
+        E *= c.inv_s;
+    }
+    R k7 = R(0);
+    if (KIN) {
+        q3 += sh[0];
+        q4 += sh[1];
+        k7 = sh[2];
+        E += sh[3];
+    }
+    const R n3 = m3 - q3;
+    const R n4 = m4 - q4;
+    const R n5 = m5 + jx;
+    const R n6 = m6 + jy;
+    const R n7 = KIN ? kfma(3, j2i, m7) - k7 : kfma(3, j2i, m7);
+    const R n8 = KIN ? m8 - (fmad(k5_3, dsum9, -kmul(3, j2i)) + k7)
+                     : m8 - fmad(k5_3, dsum9, -kmul(3, j2i));
+
+    R tau_e = c.tn, tau_m = c.te;
+    if (c.les) {
+        const R Q = sqrt_(fmad(n4, n4, kmul(4, n3 * n3)));
+        tau_e = kmul(0.5f, c.tn + sqrt_(fmad(c.k18 * Q, irho, c.tn2)));
+        const R Ny1 = g[3] - g[7];
+        const R Nx2 = g[4] - g[8];
+        const R J = fabs(Ny1 - Nx2 - kmul(2, E));
+        tau_m = kmul(0.5f, c.te + sqrt_(fmad(c.k36, J, c.te2)));
+    }
+    if (TAUS) {
+        tau_e = sh[0];
+        tau_m = sh[1];
+    }
+    const R snu = rcp(tau_e);
+    const R s7 = c.s7 > R(0) ? c.s7 : snu;
+    const R s8 = c.s8 > R(0) ? c.s8 : snu;
+
+    const R a3 = kmul(0.25f, snu * n3);
+    const R a4 = kmul(0.25f, snu * n4);
+    const R a5 = c.s5 * n5 * k1_12;
+    const R a6 = c.s6 * n6 * k1_12;
+    const R a7 = s7 * n7 * k1_180;
+    const R a8 = s8 * n8 * k1_20;
+
+    const R q78 = kfma(4, a7, -a8);
+    d[0] -= kmul(4, a7 + a8);
+    d[1] -= kfma(-5, a7, kfma(-2, a5, a4));
+    d[2] -= kfma(-5, a7, kfma(-2, a6, -a4));
+    d[3] -= kfma(-5, a7, kfma(2, a5, a4));
+    d[4] -= kfma(-5, a7, kfma(2, a6, -a4));
+    d[5] -= (a3 + a5) + (a6 + q78);
+    d[6] -= (a6 - a3) - (a5 - q78);
+    d[7] -= (a3 - a5) - (a6 - q78);
+    d[8] -= (a5 - a3) - (a6 - q78);
+
+    const R sm = rcp(tau_m);
+    const R third = k1_3, sixth = k1_6;
+    const R e3 = kmul(3, E);
+    const R geq[10] = {third * bx,        third * by,          // k = 0
+                       sixth * bx,        sixth * (by + e3),   // k = 1 (+x)
+                       sixth * (bx - e3), sixth * by,          // k = 2 (+y)
+                       sixth * bx,        sixth * (by - e3),   // k = 3 (-x)
+                       sixth * (bx + e3), sixth * by};         // k = 4 (-y)
+#pragma unroll
+    for (int q = 0; q < 10; ++q) g[q] = fmad(-sm, g[q] - geq[q], g[q]);
+}
+
 }  // namespace lbmhd

@@ -50,12 +50,16 @@ bool tma_variant_ok(int prec, int W, int nx);
 // shared-memory ring).  two_pass: conserved moments of the streamed
 // populations into `mom` (5 planes of the arithmetic type, plane stride
 // g.ps), then the step.  Both give the same bits.
-// Kinetic-LES step of an ensemble (lbmhd_kinetic.cu): the moments pass and
-// the step over every work unit, one CTA per unit.  runs: device array of
-// RunDev<R> (lbmhd_batch_run.cuh); mom: the runs' moment planes.
-cudaError_t launch_batch_kinetic(int prec, int kin, const void* runs, const int* unit_run,
-                                 unsigned nunits, int block, const void* src, void* dst,
-                                 void* mom, float inv_s, cudaStream_t st);
+// Kinetic-LES step of an ensemble (lbmhd_kinetic.cu), one CTA per work
+// unit.  fused: the one-pass kernel, a unit being one strip-segment of a run
+// (kinetic_fused_strip(prec) columns wide; RunDev::kstrips, kseglen);
+// otherwise the moments pass and the step, a unit being `block` nodes.
+// runs: device array of RunDev<R> (lbmhd_batch_run.cuh); mom: the runs'
+// moment planes (two-pass only).
+cudaError_t launch_batch_kinetic(int prec, int kin, bool fused, const void* runs,
+                                 const int* unit_run, unsigned nunits, int block, const void* src,
+                                 void* dst, void* mom, float inv_s, cudaStream_t st);
+int kinetic_fused_strip(int prec);
 cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
                                 void* dst, void* mom, const Geom& g, const HostColl& c,
                                 cudaStream_t st);

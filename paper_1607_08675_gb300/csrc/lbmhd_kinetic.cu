@@ -96,7 +96,7 @@ __device__ __forceinline__ void kin_step_node(const typename Fmt<P>::S* __restri
         if (Fmt<P>::kScaled)
 #pragma unroll
             for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
-        collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
+        collide_xf<R, Fmt<P>::kScaled, true>(d, g, c, sh);
     } else {
         // u = j / rho at the four neighbours, B as stored
         const R* m0 = mom;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void kin_step_node(const typename Fmt<P>::S* __restri
             gb[a][1] = R(0.5) * (mb[yp] - mb[ym]);
         }
         carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
-        collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
+        collide_xf<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) dst[i * ps + node] = Fmt<P>::enc(d[i], i, 1.0f);
@@ -149,29 +149,26 @@ __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S*
 // [y0, y1), and sweeps down it, keeping the conserved moments of the
 // populations streamed into consecutive rows (the sw strip nodes and the
 // two periodic halo columns x0 - 1, x0 + sw) in a ring of 5 rows in shared
-// memory.  Per row y: phase A forms the moments of row y + 1, a barrier,
-// then phase B collides row y with the central differences from the ring.
-// Phase B takes the pulled populations of its node either from registers,
-// where phase A left them one row earlier (KEEP), or by pulling again (they
-// come from L1/L2).  Every stored value is read from DRAM once, so the step
-// moves the 152 B/node (FP32) of a plain step instead of the two-pass 268 B.
-// Ring of 5 rows: phase A of row y + 2 (slot j + 3) may run while a slower
-// thread still reads rows y - 1 .. y + 1 (slots j .. j + 2) in phase B, and
-// no thread gets further ahead without passing the next barrier.  Moments,
-// differences and collision are the arithmetic of the two-pass kernels, so
-// both give the same bits.
+// memory.  Per row y: phase A pulls the populations of row y + 1 and forms
+// their moments, a barrier, then phase B collides row y with the central
+// differences from the ring and the populations phase A pulled one row
+// earlier, kept in registers.  Every stored value is read from DRAM once,
+// so the step moves the 152 B/node (FP32) of a plain step instead of the
+// two-pass 268 B.  Ring of 5 rows: phase A of row y + 2 (slot j + 3) may
+// run while a slower thread still reads rows y - 1 .. y + 1 (slots j ..
+// j + 2) in phase B, and no thread gets further ahead without passing the
+// next barrier.  Moments, differences and collision are the arithmetic of
+// the two-pass kernels, so both give the same bits.
+//
+// Addressing: plane p starts at base + p * ps; inside a plane a node is a
+// 32-bit offset y * nx + x (a lattice has at most 2^30 nodes).
+// U2: the row loop is unrolled by two with the kept populations in two
+// register sets used alternately, so no per-row copies of the 19 values.
+// Measured on GB300 at 8192^2, FP32, MLUPS (fraction of the measured copy
+// bandwidth at 152 B/node): les 2 with U2 38.8K (0.87), without 33.4K; les 3
+// without 38.4K (0.86), with 36.4K -- the register schedule decides, so the
+// choice is per closure.
 constexpr int kRing = 5;
-
-template <int P>
-__device__ __forceinline__ void load_pulled(const typename Fmt<P>::S* __restrict__ src, int x,
-                                            int y, int nx, int ny, long long ps,
-                                            typename Fmt<P>::R (&v)[kPlanes]) {
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p)
-        v[p] = Fmt<P>::dec(src[p * ps + (long long)wrapk(y - plane_cy(p), ny) * nx +
-                               wrapk(x - plane_cx(p), nx)],
-                           p, 1.0f);
-}
 
 template <int P>
 __device__ __forceinline__ void sum_moments(const typename Fmt<P>::R (&d)[kPlanes], float inv_s,
@@ -196,17 +193,16 @@ __device__ __forceinline__ void sum_moments(const typename Fmt<P>::R (&d)[kPlane
     m[4] = by;
 }
 
-template <int P, int MODE, int SW, int MINB, bool KEEP>
-__global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
-    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst, int nx,
-    int ny, long long ps, int seglen, Coll<typename Fmt<P>::R> c, float inv_s) {
+// The work of one CTA of SW + 32 threads on one strip-segment of one lattice
+// (src, dst: 19 planes of stride ps).  ring: the CTA's shared moment rows.
+template <int P, int MODE, int SW, bool U2>
+__device__ __forceinline__ void kin_fused_body(
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst,
+    long long ps, int nx, int ny, int x0, int y0, int y1, const Coll<typename Fmt<P>::R>& c,
+    float inv_s, typename Fmt<P>::R (*ring)[5][SW + 2]) {
     using R = typename Fmt<P>::R;
-    __shared__ R ring[kRing][5][SW + 2];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * SW;
     const int sw = min(SW, nx - x0);
-    const int y0 = blockIdx.y * seglen;
-    const int y1 = min(y0 + seglen, ny);
     // moment position of this thread: strip node, left halo, right halo
     int pos = -1, xm = 0;
     if (tid < sw) {
@@ -219,10 +215,24 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
         pos = sw + 1;
         xm = wrapk(x0 + sw, nx);
     }
+    const unsigned xw = (unsigned)wrapk(xm - 1, nx), xe = (unsigned)wrapk(xm + 1, nx);
+    // populations streamed into (xm, yy): plane p from (xm - c_px, yy - c_py)
+    auto pull = [&](int yy, R (&v)[kPlanes]) {
+        const unsigned rm = (unsigned)wrapk(yy - 1, ny) * (unsigned)nx;
+        const unsigned r0 = (unsigned)yy * (unsigned)nx;
+        const unsigned rp = (unsigned)wrapk(yy + 1, ny) * (unsigned)nx;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const int cx = plane_cx(p), cy = plane_cy(p);
+            const unsigned row = cy == 0 ? r0 : (cy > 0 ? rm : rp);
+            const unsigned col = cx == 0 ? (unsigned)xm : (cx > 0 ? xw : xe);
+            v[p] = Fmt<P>::dec(src[p * ps + (row + col)], p, 1.0f);
+        }
+    };
     // phase A: pulled populations of (xm, yy) into v, their moments into a slot
     auto phase_a = [&](int yy, int slot, R (&v)[kPlanes]) {
         if (pos < 0) return;
-        load_pulled<P>(src, xm, wrapk(yy, ny), nx, ny, ps, v);
+        pull(wrapk(yy, ny), v);
         R m[5];
         sum_moments<P>(v, inv_s, m);
 #pragma unroll
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
     // phase B: collide node (x0 + tid, y), pulled populations in v, with the
     // moment rows y - 1, y, y + 1 in slots sm, s0, sp
     auto phase_b = [&](int y, int sm, int s0, int sp, const R (&v)[kPlanes]) {
-        const int x = x0 + tid, i = tid + 1;
+        const int i = tid + 1;
         R d[9], g[10];
 #pragma unroll
         for (int p = 0; p < 9; ++p) d[p] = v[p];
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
             if (Fmt<P>::kScaled)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) sh[q] *= c.scl;
-            collide<R, Fmt<P>::kScaled, true>(d, g, c, sh);
+            collide_xf<R, Fmt<P>::kScaled, true>(d, g, c, sh);
         } else {
             const R ixp = recip(ring[s0][0][i + 1]), ixm = recip(ring[s0][0][i - 1]),
                     iyp = recip(ring[sp][0][i]), iym = recip(ring[sm][0][i]);
@@ -262,55 +272,84 @@ __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
                 gb[a][1] = R(0.5) * (ring[sp][3 + a][i] - ring[sm][3 + a][i]);
             }
             carati_taus<R>(gu, gb, c.cd2, c.tn, c.te, taus);
-            collide<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
+            collide_xf<R, Fmt<P>::kScaled, false, true>(d, g, c, taus);
         }
-        const long long node = (long long)y * nx + x;
+        const unsigned node = (unsigned)y * (unsigned)nx + (unsigned)xm;
 #pragma unroll
         for (int q = 0; q < 9; ++q) dst[q * ps + node] = Fmt<P>::enc(d[q], q, 1.0f);
 #pragma unroll
         for (int q = 0; q < 10; ++q) dst[(9 + q) * ps + node] = Fmt<P>::enc(g[q], 9 + q, 1.0f);
     };
-    R cur[kPlanes];
-    phase_a(y0 - 1, 0, cur);
-    phase_a(y0, 1, cur);
-    for (int y = y0, j = 0; y < y1; ++y, ++j) {
-        R nxt[kPlanes];
+    R va[kPlanes], vb[kPlanes];
+    phase_a(y0 - 1, 0, va);
+    phase_a(y0, 1, va);
+    // one row: moments of row y + 1 (pulled into nxt), barrier, collide row
+    // y (pulled into cur one row earlier)
+    auto row = [&](int y, int j, R (&cur)[kPlanes], R (&nxt)[kPlanes]) {
         phase_a(y + 1, (j + 2) % kRing, nxt);
         __syncthreads();
-        if (tid < sw) {
-            if (!KEEP) load_pulled<P>(src, x0 + tid, y, nx, ny, ps, cur);
-            phase_b(y, j % kRing, (j + 1) % kRing, (j + 2) % kRing, cur);
+        if (tid < sw) phase_b(y, j % kRing, (j + 1) % kRing, (j + 2) % kRing, cur);
+    };
+    if (U2) {
+        int y = y0, j = 0;
+        for (; y + 1 < y1; y += 2, j += 2) {
+            row(y, j, va, vb);
+            row(y + 1, j + 1, vb, va);
         }
-        if (KEEP)
+        if (y < y1) row(y, j, va, vb);
+    } else {
+        for (int y = y0, j = 0; y < y1; ++y, ++j) {
+            row(y, j, va, vb);
 #pragma unroll
-            for (int p = 0; p < kPlanes; ++p) cur[p] = nxt[p];
+            for (int p = 0; p < kPlanes; ++p) va[p] = vb[p];
+        }
     }
 }
 
-// SW: strip width; MINB: CTAs per SM the register budget is sized for;
-// KEEP: phase B takes its populations from registers.  Measured on GB300 at
-// 8192^2 (FP32, les = 2, MLUPS, with FMA contraction): strip 256 / 3 CTAs /
-// KEEP 35.3K; without KEEP 33.0K; strips of 128 or 96 with more CTAs per SM
-// 29-34K; a variant that issued the next row's loads before phase B (4-row
-// ring) 25-28K (register spills); the two-pass kernels 23.9K.  Without FMA
-// contraction (as built): 33.5K, two-pass 23.7K.
-template <int P, int SW, int MINB, bool KEEP>
+template <int P, int MODE, int SW, int MINB, bool U2>
+__global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst, int nx,
+    int ny, long long ps, int seglen, Coll<typename Fmt<P>::R> c, float inv_s) {
+    using R = typename Fmt<P>::R;
+    __shared__ R ring[kRing][5][SW + 2];
+    const int y0 = blockIdx.y * seglen;
+    kin_fused_body<P, MODE, SW, U2>(src, dst, ps, nx, ny, blockIdx.x * SW, y0,
+                                    min(y0 + seglen, ny), c, inv_s, ring);
+}
+
+// Fused-kernel shape per format: strip width SW (FP64 and FF hold twice the
+// registers per value), CTAs per SM the register budget is sized for, and
+// the two-row unroll for the filtered equilibria (les 2).
+template <int P>
+struct FusedShape {
+    static constexpr bool kWide = P == P_FP64 || P == P_FF;
+    static constexpr int SW = kWide ? 128 : 256;
+    static constexpr int MINB = kWide ? 2 : 3;
+};
+
+// Row segments per strip for about four waves of resident CTAs; each
+// segment forms two moment rows again.
+inline int fused_seglen(int nx, int ny, int sw, int minb, int sm_count) {
+    const int nstrips = (nx + sw - 1) / sw;
+    const long long want = 4LL * minb * (sm_count > 0 ? sm_count : 1);
+    long long nseg = (want + nstrips - 1) / nstrips;
+    if (nseg > ny) nseg = ny;
+    if (nseg < 1) nseg = 1;
+    return (int)((ny + nseg - 1) / nseg);
+}
+
+template <int P>
 cudaError_t launch_fused(const void* src, void* dst, const Geom& g, const HostColl& hc,
                          int sm_count, cudaStream_t st) {
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
+    constexpr int SW = FusedShape<P>::SW, MINB = FusedShape<P>::MINB;
     const int nstrips = (g.nx + SW - 1) / SW;
-    // about four waves of MINB resident CTAs per SM; each row segment
-    // re-forms two moment rows
-    const long long want = 4LL * MINB * (sm_count > 0 ? sm_count : 1);
-    long long nseg = (want + nstrips - 1) / nstrips;
-    if (nseg > g.ny) nseg = g.ny;
-    if (nseg < 1) nseg = 1;
-    const int seglen = (int)((g.ny + nseg - 1) / nseg);
-    nseg = (g.ny + seglen - 1) / seglen;
+    const int seglen = fused_seglen(g.nx, g.ny, SW, MINB, sm_count);
+    const int nseg = (g.ny + seglen - 1) / seglen;
     const dim3 grid((unsigned)nstrips, (unsigned)nseg);
-    auto k = hc.kin == 3 ? step_kin_fused_kernel<P, 3, SW, MINB, KEEP>
-                         : step_kin_fused_kernel<P, 2, SW, MINB, KEEP>;
+    auto k = hc.kin == 3 ? step_kin_fused_kernel<P, 3, SW, MINB, false>
+                         : step_kin_fused_kernel<P, 2, SW, MINB, true>;
     k<<<grid, SW + 32, 0, st>>>((const S*)src, (S*)dst, g.nx, g.ny, g.ps, seglen,
                                 coll_for_prec<R>(hc, P), hc.inv_scale);
     return cudaGetLastError();
@@ -342,13 +381,39 @@ __global__ void __launch_bounds__(256) batch_kin_step_kernel(
                                rd.c);
 }
 
+// The fused kernel over an ensemble: one CTA per work unit, a unit being one
+// strip-segment of one run (unit_run gives the run; the unit's place in the
+// run's strips x segments follows from the run's first unit), so every run
+// evolves bit-identically to its own lattice.
+template <int P, int MODE, int SW, int MINB, bool U2>
+__global__ void __launch_bounds__(SW + 32, MINB) batch_kin_fused_kernel(
+    const RunDev<typename Fmt<P>::R>* __restrict__ runs, const int* __restrict__ unit_run,
+    const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst,
+    float inv_s) {
+    using R = typename Fmt<P>::R;
+    __shared__ R ring[kRing][5][SW + 2];
+    const RunDev<R>& rd = runs[unit_run[blockIdx.x]];
+    const int l = (int)(blockIdx.x - rd.unit0);
+    const int strip = l % rd.kstrips, seg = l / rd.kstrips;
+    const int y0 = seg * rd.kseglen;
+    kin_fused_body<P, MODE, SW, U2>(src + rd.off, dst + rd.off, rd.ps, rd.nx, rd.ny, strip * SW,
+                                    y0, min(y0 + rd.kseglen, rd.ny), rd.c, inv_s, ring);
+}
+
 template <int P>
-cudaError_t launch_batch_p(int kin, const void* runs, const int* unit_run, unsigned nunits,
-                           int block, const void* src, void* dst, void* mom, float inv_s,
-                           cudaStream_t st) {
+cudaError_t launch_batch_p(int kin, bool fused, const void* runs, const int* unit_run,
+                           unsigned nunits, int block, const void* src, void* dst, void* mom,
+                           float inv_s, cudaStream_t st) {
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
     const RunDev<R>* rd = (const RunDev<R>*)runs;
+    if (fused) {
+        constexpr int SW = FusedShape<P>::SW, MINB = FusedShape<P>::MINB;
+        auto k = kin == 3 ? batch_kin_fused_kernel<P, 3, SW, MINB, false>
+                          : batch_kin_fused_kernel<P, 2, SW, MINB, true>;
+        k<<<nunits, SW + 32, 0, st>>>(rd, unit_run, (const S*)src, (S*)dst, inv_s);
+        return cudaGetLastError();
+    }
     batch_kin_moments_kernel<P><<<nunits, block, 0, st>>>(rd, unit_run, (const S*)src, (R*)mom,
                                                           inv_s);
     cudaError_t e = cudaGetLastError();
@@ -381,19 +446,33 @@ cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const
 
 }  // namespace
 
-cudaError_t launch_batch_kinetic(int prec, int kin, const void* runs, const int* unit_run,
-                                 unsigned nunits, int block, const void* src, void* dst,
-                                 void* mom, float inv_s, cudaStream_t st) {
+cudaError_t launch_batch_kinetic(int prec, int kin, bool fused, const void* runs,
+                                 const int* unit_run, unsigned nunits, int block, const void* src,
+                                 void* dst, void* mom, float inv_s, cudaStream_t st) {
+#define LBMHD_KB(P)                                                                             \
+    case P:                                                                                     \
+        return launch_batch_p<P>(kin, fused, runs, unit_run, nunits, block, src, dst, mom, inv_s, \
+                                 st);
     switch (prec) {
-        case P_FP64: return launch_batch_p<P_FP64>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
-        case P_FP32: return launch_batch_p<P_FP32>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
-        case P_FP32_DEV:
-            return launch_batch_p<P_FP32_DEV>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
-        case P_FP16_DEV:
-            return launch_batch_p<P_FP16_DEV>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
-        case P_FF: return launch_batch_p<P_FF>(kin, runs, unit_run, nunits, block, src, dst, mom, inv_s, st);
+        LBMHD_KB(P_FP64)
+        LBMHD_KB(P_FP32)
+        LBMHD_KB(P_FP32_DEV)
+        LBMHD_KB(P_FP16_DEV)
+        LBMHD_KB(P_FF)
     }
+#undef LBMHD_KB
     return cudaErrorInvalidValue;
+}
+
+int kinetic_fused_strip(int prec) {
+    switch (prec) {
+        case P_FP64: return FusedShape<P_FP64>::SW;
+        case P_FF: return FusedShape<P_FF>::SW;
+        case P_FP32: return FusedShape<P_FP32>::SW;
+        case P_FP32_DEV: return FusedShape<P_FP32_DEV>::SW;
+        case P_FP16_DEV: return FusedShape<P_FP16_DEV>::SW;
+    }
+    return 0;
 }
 
 cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
@@ -401,13 +480,11 @@ cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const voi
                                 cudaStream_t st) {
     if (!two_pass) {
         switch (prec) {
-            case P_FP64: return launch_fused<P_FP64, 128, 2, true>(src, dst, g, c, sm_count, st);
-            case P_FP32: return launch_fused<P_FP32, 256, 3, true>(src, dst, g, c, sm_count, st);
-            case P_FP32_DEV:
-                return launch_fused<P_FP32_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
-            case P_FP16_DEV:
-                return launch_fused<P_FP16_DEV, 256, 3, true>(src, dst, g, c, sm_count, st);
-            case P_FF: return launch_fused<P_FF, 128, 2, true>(src, dst, g, c, sm_count, st);
+            case P_FP64: return launch_fused<P_FP64>(src, dst, g, c, sm_count, st);
+            case P_FP32: return launch_fused<P_FP32>(src, dst, g, c, sm_count, st);
+            case P_FP32_DEV: return launch_fused<P_FP32_DEV>(src, dst, g, c, sm_count, st);
+            case P_FP16_DEV: return launch_fused<P_FP16_DEV>(src, dst, g, c, sm_count, st);
+            case P_FF: return launch_fused<P_FF>(src, dst, g, c, sm_count, st);
         }
         return cudaErrorInvalidValue;
     }

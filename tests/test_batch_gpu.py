@@ -23,6 +23,7 @@ RUNS = [  # (nx, ny, tau_nu, tau_eta, C_S)
     (64, 64, 0.7, 0.6, 0.05),
     (192, 40, 0.55, 0.58, 0.15),
     (128, 1, 0.6, 0.6, 0.10),
+    (300, 130, 0.58, 0.6, 0.12),  # a ragged third strip, two row segments
 ]
 
 
@@ -171,28 +172,31 @@ def test_batch_rejects_bad_runs(L):
     L.lbmhd_batch_destroy(b)
 
 
+@pytest.mark.parametrize("kernel", [1, 0])
 @pytest.mark.parametrize("les", [2, 3])
 @pytest.mark.parametrize("prec", ["fp32", "fp16_dev", "fp64", "ff"])
-def test_kinetic_ensemble_runs_equal_single_lattices_bitwise(L, prec, les):
+def test_kinetic_ensemble_runs_equal_single_lattices_bitwise(L, prec, les, kernel):
     """Ensembles of the paper's kinetic LES (les 2) and of the cross-helicity
-    closure (les 3): a moments pass and the step over every run's work units
-    per step, the two-pass kernels' per-node code, so every run equals its
-    own lattice bit for bit, through graph replays and a direct tail.  The
-    shape is one node per thread and one step per launch; others are
-    refused."""
+    closure (les 3), one step per launch: the fused kernel over every run's
+    strip-segments (vec 1) or the moments pass and the step over every
+    run's nodes (vec 0).  Either way every run equals its own lattice bit
+    for bit, through graph replays and a direct tail.  The default is the
+    single lattice's choice (two-pass for FP64, and for FF with les 2);
+    other shapes are refused."""
     nx, ny, tn, te, cs = zip(*RUNS)
     common = L.lbmhd_params_default(precision=prec, les=les, delta=2.0)
     b = L.lbmhd_batch_create(nx, ny, tn, te, cs, common)
     vec, block, spl = L.lbmhd_batch_get_launch(b)
-    assert vec == 1 and spl == 1
-    for bad in ((2, 64, 1), (1, 64, 8)):
+    two_pass = prec == "fp64" or (prec == "ff" and les == 2)
+    assert vec == (0 if two_pass else 1) and spl == 1
+    for bad in ((2, 64, 1), (1, 64, 8), (4, 64, 1)):
         with pytest.raises(L.LBMHDError):
             L.lbmhd_batch_set_launch(b, *bad)
-    if prec == "fp32":  # the autotuner keeps to the allowed shapes
+    if prec == "fp32" and kernel == 1:  # the autotuner keeps to the allowed shapes
         assert L.lbmhd_batch_autotune(b, None, 4) > 0
         vec, block, spl = L.lbmhd_batch_get_launch(b)
-        assert vec == 1 and spl == 1
-    L.lbmhd_batch_set_launch(b, 1, 64, 1)
+        assert vec in (0, 1) and spl == 1
+    L.lbmhd_batch_set_launch(b, kernel, 64, 1)
     fields = [inputs.orszag_tang(r[0], r[1], seed=20 + i) for i, r in enumerate(RUNS)]
     for i, f in enumerate(fields):
         L.lbmhd_batch_init(b, i, *f)
@@ -206,5 +210,5 @@ def test_kinetic_ensemble_runs_equal_single_lattices_bitwise(L, prec, les):
         L.lbmhd_step(h, steps)
         ref = L.lbmhd_get_state(h)
         L.lbmhd_destroy(h)
-        assert np.array_equal(L.lbmhd_batch_get_state(b, i), ref), (prec, les, i)
+        assert np.array_equal(L.lbmhd_batch_get_state(b, i), ref), (prec, les, kernel, i)
     L.lbmhd_batch_destroy(b)
