@@ -255,6 +255,9 @@ int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
  * out = device pointer to 12 doubles, written in the field order of
  * lbmhd_diag (mass ... current_sq); stream = cudaStream_t (NULL: legacy
  * default stream).  Enqueued on the stream; does not synchronise.
+ * Alignment: state on a multiple of the stored value size (8 bytes for
+ * FP64 and FF, 4 for FP32 and FP32_DEV, 2 for FP16_DEV), out on 8 bytes;
+ * other pointers get EINVAL before anything is launched.
  * The per-block partial sums live in one static device array of 96 KiB
  * (1024 rows of 12 doubles), held by every GPU that loads the library
  * until the process exits; every lattice the library accepts
@@ -266,8 +269,8 @@ int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block);
  * array: calls that overlap on the GPU (other streams, other threads)
  * race and give wrong sums; serialise them.  Each call writes every
  * partial row it reads, so no clearing is needed between calls.
- * Errors: EINVAL for NULL pointers, an unknown precision, bad sizes or
- * scale; ECUDA if the address lookup or the launch fails. */
+ * Errors: EINVAL for NULL or misaligned pointers, an unknown precision,
+ * bad sizes or scale; ECUDA if the address lookup or the launch fails. */
 int lbmhd_diagnostics_noalloc(const void* state, int precision, int nx, int ny,
                               long long plane_stride, double fp16_scale, double* out,
                               void* stream);
@@ -329,9 +332,12 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * with the same parameters.  The grid-barrier wait is bounded (about one
  * second); on expiry the step reports LBMHD_ETIMEOUT at the next
  * synchronising call and every run must be re-initialised.
- * With les = 2 or 3 (common->les) each step is a moments pass and the step
- * over every run's work units (one node per thread, one step per launch,
- * no grid barrier), and the batch holds five moment planes per run. */
+ * With les = 2 or 3 (common->les) each step is one launch with no grid
+ * barrier: the fused kinetic kernel over every run's strip-segments (one CTA
+ * per segment of a column strip of a run; vec 1), or the moments pass and
+ * the step over every run's nodes (vec 0, `block` nodes per unit); the batch
+ * holds five moment planes per run for the latter.  The default is the
+ * single lattice's choice: two-pass for FP64, and for FF with les 2. */
 typedef struct lbmhd_batch_t lbmhd_batch_t;
 
 /* Arrays of nruns entries (caller-owned, not retained).  Every run is
@@ -361,7 +367,8 @@ int lbmhd_batch_sync(lbmhd_batch_t* b);
 /* Work shape: vec nodes per thread (1, 2, 4; must divide every run's nx),
  * block threads per work unit (multiple of 32, <= 256), steps per
  * persistent launch (1..4096).  Results do not depend on the shape.
- * Ensembles with les 2 or 3 take vec 1 and one step per launch only. */
+ * Ensembles with les 2 or 3 take one step per launch and vec 1 (the fused
+ * kernel; block is then not used) or vec 0 (the two-pass kernels). */
 int lbmhd_batch_set_launch(lbmhd_batch_t* b, int vec, int block, int steps_per_launch);
 int lbmhd_batch_get_launch(const lbmhd_batch_t* b, int* vec, int* block, int* steps_per_launch);
 

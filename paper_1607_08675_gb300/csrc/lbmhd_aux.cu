@@ -2,8 +2,10 @@
 // the non-finite check and the FP64 diagnostics reduction.
 #include "lbmhd_cp_async.cuh"
 #include "lbmhd_device.cuh"
+#include "lbmhd_diag_plan.h"
 #include "lbmhd_internal.h"
 
+#include <mutex>
 #include <type_traits>
 
 namespace lbmhd {
@@ -174,7 +176,7 @@ __global__ void finite_kernel(const typename Fmt<P>::S* __restrict__ st, int* fl
 // The thread sums then go to FP64: fixed warp-shuffle tree -> fixed
 // cross-warp order -> one partial row per block; a single-block pass
 // combines the rows in block order.  Same lattice, same result, bit for bit.
-constexpr int kOwn = 30, kDiagWarps = 8, kDiagBlocks = 1024, kNQ = 12;
+constexpr int kNQ = 12;  // kOwn, kDiagWarps, kDiagBlocks: lbmhd_diag_plan.h
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -258,38 +260,6 @@ __device__ __forceinline__ ff shfl_dn_r(ff v) { return ff(shfl_dn_r(v.hi), shfl_
 // (plus the halo columns and two rows per segment) from the 19 values
 // stored at it.  No barrier: a warp's stored values pass through its own
 // ring of rows (below).
-struct DiagPlan {
-    int nstrips, nseg, seglen, nblocks;
-    long long nunits;
-};
-// The work is cut into units of one warp each, a whole number of waves of
-// the kernel's resident warps and at least kDiagMinWarps warps per SM (the
-// fastest split at 8192^2 for every ring depth and residency tried: fewer
-// warps leave the memory system short of requests, a part-filled last
-// wave leaves SMs idle).
-constexpr int kDiagMinWarps = 48;
-inline DiagPlan diag_plan(const Geom& g, long long resident_warps, int nsm) {
-    DiagPlan d;
-    d.nstrips = (g.nx + kOwn - 1) / kOwn;
-    const long long want = (long long)kDiagMinWarps * nsm;
-    const long long cap = (long long)kDiagBlocks * kDiagWarps;  // partial rows
-    long long target = cap;
-    if (resident_warps < cap) {
-        long long waves = (want + resident_warps - 1) / resident_warps;
-        if (waves * resident_warps > cap) waves = cap / resident_warps;  // whole waves only
-        target = waves * resident_warps;
-    }
-    if (target < kDiagWarps) target = kDiagWarps;
-    long long nseg = target / d.nstrips;
-    if (nseg > g.ny) nseg = g.ny;
-    if (nseg < 1) nseg = 1;
-    d.seglen = (int)((g.ny + nseg - 1) / nseg);
-    d.nseg = (int)((g.ny + d.seglen - 1) / d.seglen);
-    d.nunits = (long long)d.nstrips * d.nseg;
-    const long long warps = d.nunits < target ? d.nunits : target;
-    d.nblocks = (int)((warps + kDiagWarps - 1) / kDiagWarps);
-    return d;
-}
 
 // Rows of stored values in flight per warp.  4- and 8-byte values are
 // staged by asynchronous copies (cp.async) into a per-warp ring of
@@ -652,30 +622,50 @@ cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Ge
     return cudaGetLastError();
 }
 
-// Warps of diag_kernel<P, WIDE> resident on the device at once (the
+// Warps of diag_kernel<P, WIDE> resident on the current device at once (the
 // kernel's registers and ring bound its blocks per SM), found once per
-// process.
+// device: a process may drive GPUs with different SM counts.
 struct DiagOcc {
     long long warps;  // resident warps of the kernel on the device
     int nsm;
 };
+constexpr int kOccDevices = 64;
 template <int P, bool WIDE>
 static DiagOcc diag_occupancy() {
-    static const DiagOcc o = [] {
+    static std::mutex mu;
+    static DiagOcc cache[kOccDevices];
+    static bool have[kOccDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto query = [dev] {
         constexpr size_t smem = diag_smem_bytes<P, WIDE>();
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(diag_kernel<P, WIDE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, nsm = 0, bps = 0;
-        cudaGetDevice(&dev);
+        int nsm = 0, bps = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, diag_kernel<P, WIDE>,
                                                       32 * kDiagWarps, smem);
         cudaGetLastError();  // a failed query leaves the floors below
         nsm = nsm > 0 ? nsm : 1;
         return DiagOcc{(long long)nsm * (bps > 0 ? bps : 1) * kDiagWarps, nsm};
-    }();
-    return o;
+    };
+    if (dev < 0 || dev >= kOccDevices) return query();
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[dev]) {
+        cache[dev] = query();
+        have[dev] = true;
+    }
+    return cache[dev];
+}
+
+// The 4-byte formats have two forms of the kernel; both take the plan of the
+// form with fewer resident warps, so that one lattice is cut the same way,
+// and gives the same bits, whichever form its layout selects.
+template <int P>
+static DiagOcc diag_occupancy_shared() {
+    const DiagOcc a = diag_occupancy<P, true>(), b = diag_occupancy<P, false>();
+    return a.warps < b.warps ? a : b;
 }
 
 // The wide form serves 4-byte storage whose rows and planes start on
@@ -685,30 +675,21 @@ static bool diag_wide(int prec, const Geom& g, const void* state) {
            ((uintptr_t)state & 15) == 0;
 }
 
-static DiagPlan diag_plan_for(const Geom& g, int prec, bool wide) {
+static DiagPlan diag_plan_for(const Geom& g, int prec) {
     DiagOcc o{kDiagWarps, 1};
     switch (prec) {
         case P_FP64: o = diag_occupancy<P_FP64, false>(); break;
-        case P_FP32:
-            o = wide ? diag_occupancy<P_FP32, true>() : diag_occupancy<P_FP32, false>();
-            break;
-        case P_FP32_DEV:
-            o = wide ? diag_occupancy<P_FP32_DEV, true>() : diag_occupancy<P_FP32_DEV, false>();
-            break;
+        case P_FP32: o = diag_occupancy_shared<P_FP32>(); break;
+        case P_FP32_DEV: o = diag_occupancy_shared<P_FP32_DEV>(); break;
         case P_FP16_DEV: o = diag_occupancy<P_FP16_DEV, false>(); break;
         case P_FF: o = diag_occupancy<P_FF, false>(); break;
         default: break;
     }
-    return diag_plan(g, o.warps, o.nsm);
+    return diag_plan(g.nx, g.ny, o.warps, o.nsm);
 }
 
-// Partial rows a reduction of this lattice may need (either form).
-int diag_num_blocks(const Geom& g, int prec) {
-    const int a = diag_plan_for(g, prec, false).nblocks;
-    const bool w = prec == P_FP32 || prec == P_FP32_DEV;
-    const int b = w ? diag_plan_for(g, prec, true).nblocks : a;
-    return a > b ? a : b;
-}
+// Partial rows a reduction of this lattice needs on the current device.
+int diag_num_blocks(const Geom& g, int prec) { return diag_plan_for(g, prec).nblocks; }
 
 template <int P, bool WIDE>
 static cudaError_t diag_launch_p(const void* state, double* partials, const Geom& g,
@@ -728,7 +709,7 @@ static cudaError_t diag_launch_p(const void* state, double* partials, const Geom
 cudaError_t launch_diag(int prec, const void* state, double* partials, double* out12,
                         const Geom& g, const HostColl& c, cudaStream_t st) {
     const bool wide = diag_wide(prec, g, state);
-    const DiagPlan d = diag_plan_for(g, prec, wide);
+    const DiagPlan d = diag_plan_for(g, prec);
     const int nb = d.nblocks;
     cudaError_t e = cudaSuccess;
     if (wide && prec == P_FP32)

@@ -7,6 +7,8 @@
 // device synchronisation of cudaMalloc / cudaFree.  For them the FP64
 // diagnostics reduction runs here with its per-block partial sums in a
 // fixed, file-scope device array instead of memory from lbmhd_create.
+#include <stdint.h>
+
 #include <mutex>
 
 #include "lbmhd_internal.h"
@@ -69,6 +71,18 @@ extern "C" int lbmhd_diagnostics_noalloc(const void* state, int precision, int n
     }
     if (storage_bytes(precision) == 0) {
         set_error("unknown precision");
+        return LBMHD_EINVAL;
+    }
+    // A pointer carved out of a caller's arena may sit anywhere; the kernel
+    // reads whole stored values and writes FP64 sums, so misalignment is
+    // refused here, before anything reaches the GPU.
+    if ((uintptr_t)state % storage_bytes(precision) != 0) {
+        set_error("state must be aligned to the stored value size (8 B FP64 / FF, 4 B FP32, "
+                  "2 B FP16)");
+        return LBMHD_EINVAL;
+    }
+    if ((uintptr_t)out % sizeof(double) != 0) {
+        set_error("out must be 8-byte aligned");
         return LBMHD_EINVAL;
     }
     if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 30)) {

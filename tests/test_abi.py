@@ -92,3 +92,21 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower() or f == "inputs.py", f
+
+
+def test_noalloc_diagnostics_refuses_misaligned_pointers_on_the_host(L):
+    """lbmhd_diagnostics_noalloc checks pointer alignment before any CUDA
+    call, so the refusal needs no GPU: a state off the stored value size or
+    an out pointer off 8 bytes is EINVAL (the addresses are never touched)."""
+    lib = L.lib()
+    base = 1 << 20  # an aligned fake address; nothing dereferences it
+    for prec, size in ((0, 8), (4, 8), (1, 4), (2, 4), (3, 2)):
+        for off in sorted({1, size // 2} - {0}):
+            rc = lib.lbmhd_diagnostics_noalloc(ctypes.c_void_p(base + off), prec, 8, 4, 32,
+                                               1024.0, ctypes.c_void_p(base), None)
+            assert rc == -1, (prec, off)
+            assert "aligned" in lib.lbmhd_last_error().decode()
+    for off in (1, 2, 4):
+        rc = lib.lbmhd_diagnostics_noalloc(ctypes.c_void_p(base), 0, 8, 4, 32, 1024.0,
+                                           ctypes.c_void_p(base + off), None)
+        assert rc == -1 and "aligned" in lib.lbmhd_last_error().decode()

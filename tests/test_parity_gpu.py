@@ -190,9 +190,10 @@ def test_diagnostics_ragged_shapes_match_oracle(L, orc, prec, shape):
     a ragged last set of columns, and a 30007 x 53 lattice whose 1001
     strips are cut into segments of several rows with a shorter last one
     (53 is prime), so a warp's row ring wraps several times per segment;
-    and 16-byte aligned rows (nx = 4, 8, 248), where the FP32 and FP16 forms
-    copy aligned windows whose granules wrap around short rows more than
-    once, with a ragged last strip at 248.  Bars: the format's relative
+    and 16-byte aligned rows (nx = 4, 8, 248), where the FP32 form copies
+    aligned windows whose granules wrap around short rows more than once,
+    with a ragged last strip at 248 (FP16 loads per lane whatever the
+    alignment).  Bars: the format's relative
     bar on every quantity; the sums of rho u and B to that bar times the
     mass (FP32 forms: 1e-9 of it); div B to the bar times the rms B."""
     nx, ny = shape

@@ -65,9 +65,11 @@ def test_noalloc_every_stored_format_bitwise(L, prec, pad, shape):
     """The raw stored state of every format, laid out with a plane stride of
     nx*ny + pad elements: the handle's own diagnostics bit for bit -- the
     same work split and arithmetic over the same values.  With nx = 128 the
-    handle and the unpadded layout take the reduction's wide form (16-byte
-    copies of aligned row windows, FP32 and FP16), the padded one (plane
-    starts off 16-byte boundaries) its per-lane copies; nx = 123 takes the
+    4-byte formats (FP32, FP32 deviations) take the reduction's wide form
+    (16-byte copies of aligned row windows) in the handle and the unpadded
+    layout, and its per-lane copies in the padded one (plane starts off
+    16-byte boundaries); FP16 always loads its values per lane into
+    registers, FP64 and FF always copy per lane; nx = 123 takes the
     per-lane form throughout."""
     import torch
 
@@ -90,6 +92,58 @@ def test_noalloc_every_stored_format_bitwise(L, prec, pad, shape):
     got = out.cpu().numpy()
     for q, key in enumerate(L.DIAG_KEYS):
         assert got[q] == ref[key], (prec, pad, key, got[q], ref[key])
+
+
+def test_noalloc_wide_and_per_lane_forms_share_one_split(L):
+    """FP32 at 2048^2, where the number of resident warps (not the row
+    count) bounds the work split: the handle's state (16-byte aligned, the
+    wide form) and the same values with planes off 16-byte boundaries (the
+    per-lane form) give the same bits, because both forms take one plan."""
+    import torch
+
+    nx = ny = 2048
+    h = L.lbmhd_create(nx, ny, L.lbmhd_params_default(precision="fp32"))
+    L.lbmhd_init(h, *inputs.turbulence(nx, ny, kmin=4, kmax=8, seed=11))
+    L.lbmhd_step(h, 5)
+    ref = L.lbmhd_diagnostics(h)
+    raw = L.lbmhd_get_state_raw(h)
+    L.lbmhd_destroy(h)
+    for pad in (0, 1):
+        ps = nx * ny + pad
+        buf = torch.zeros((19, ps), dtype=torch.float32)
+        buf[:, : nx * ny] = torch.from_numpy(raw.reshape(19, nx * ny))
+        state = buf.cuda()
+        out = torch.full((12,), float("nan"), dtype=torch.float64, device="cuda")
+        L.lbmhd_diagnostics_noalloc(state, "fp32", nx, ny, ps, out)
+        got = out.cpu().numpy()
+        for q, key in enumerate(L.DIAG_KEYS):
+            assert got[q] == ref[key], (pad, key, got[q], ref[key])
+
+
+def test_noalloc_rejects_misaligned_pointers(L):
+    """A state pointer off the stored value size, or an out pointer off 8
+    bytes (as a caller's arena may hand out), is refused with EINVAL before
+    any launch; the properly aligned call on the same buffers works."""
+    import torch
+
+    nx, ny = 8, 4
+    out = torch.zeros(16, dtype=torch.float64, device="cuda")
+    for prec, size in (("fp64", 8), ("ff", 8), ("fp32", 4), ("fp16_dev", 2)):
+        st = torch.zeros(19 * nx * ny * size + 64, dtype=torch.uint8, device="cuda")
+        for off in sorted({1, size // 2} - {0}):
+            with pytest.raises(L.LBMHDError) as e:
+                L.lbmhd_diagnostics_noalloc(st.data_ptr() + off, prec, nx, ny, nx * ny,
+                                            out.data_ptr())
+            assert e.value.code == -1
+    st = torch.zeros(19 * nx * ny + 1, dtype=torch.float64, device="cuda")
+    for off in (1, 4):
+        with pytest.raises(L.LBMHDError) as e:
+            L.lbmhd_diagnostics_noalloc(st, "fp64", nx, ny, nx * ny, out.data_ptr() + off)
+        assert e.value.code == -1
+    # one double in: every plane and the 12 sums still inside their buffers
+    L.lbmhd_diagnostics_noalloc(st.data_ptr() + 8, "fp64", nx, ny, nx * ny, out.data_ptr() + 8)
+    torch.cuda.synchronize()
+    assert out[1:13].cpu().numpy()[0] == 0.0  # mass of an all-zero state
 
 
 def test_noalloc_rejects_oversized_and_bad_arguments(L):
