@@ -134,24 +134,63 @@ def cpu_count():
         return os.cpu_count() or 1
 
 
-def time_oracle(budget_s: float = 15.0, n: int = 512):
-    """The FP64 CPU oracle, as it stands, on an n x n lattice of the same
-    recipe, all host cores; returns (MLUPS, steps, cores)."""
+# The oracle's sample of the bench workload: one lattice of the same
+# turbulence recipe and rates for the cpu_baseline figures and for the
+# reference arm (the 8192^2 lattice does not fit the oracle's time budget).
+ORACLE_SAMPLE_N = 512
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample():
     from oracle import oracle
     from paper_1607_08675_gb300 import inputs
 
     oracle.build()
-    cores = cpu_count()
-    st = oracle.init(*inputs.turbulence(n, n, seed=1))
+    n = ORACLE_SAMPLE_N
     p = oracle.params(tau_nu=0.51, tau_eta=0.51, C_S=0.1, **TURB_RATES)
-    t0 = time.perf_counter()
-    st = oracle.step(st, p, 1, nthreads=cores)
-    one = time.perf_counter() - t0
-    steps = max(1, int(budget_s / max(one, 1e-6)))
-    t0 = time.perf_counter()
-    oracle.step(st, p, steps, nthreads=cores)
-    dt = time.perf_counter() - t0
-    return n * n * steps / dt / 1e6, steps, cores, dt
+    return oracle, p, oracle.init(*inputs.turbulence(n, n, seed=1))
+
+
+def time_oracle(budget_s: float = 15.0):
+    """The FP64 CPU oracle, as it stands, on the ORACLE_SAMPLE_N^2 sample:
+    one thread for a third of the budget, then every host core (the same
+    bits either way).  Returns a cpu_baseline record."""
+    oracle, p, st = oracle_sample()
+    n = ORACLE_SAMPLE_N
+    cores = cpu_count()
+    out = {}
+    for key, threads, share in (("value_1thread", 1, 1 / 3), ("value_allcores", cores, 2 / 3)):
+        t0 = time.perf_counter()
+        st = oracle.step(st, p, 1, nthreads=threads)
+        one = time.perf_counter() - t0
+        steps = max(1, int(budget_s * share / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        st = oracle.step(st, p, steps, nthreads=threads)
+        dt = time.perf_counter() - t0
+        out[key] = n * n * steps / dt / 1e6
+        out[key.replace("value", "steps")] = steps
+        out[key.replace("value", "seconds")] = dt
+    return {"value": out["value_allcores"], "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), **out,
+            "sample": f"{n}x{n} lattice of the same turbulence recipe and rates, FP64 oracle "
+                      f"steps on 1 thread and on {cores} threads (value = all cores)"}
 
 
 def run_reference(args):
@@ -162,27 +201,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import oracle
-    from paper_1607_08675_gb300 import inputs
-
-    oracle.build()
+    oracle, p, st = oracle_sample()
+    n = ORACLE_SAMPLE_N
     cores = cpu_count()
-    p = oracle.params(tau_nu=0.51, tau_eta=0.51, C_S=0.1, **TURB_RATES)
-    per_step = min(0.5, 120.0 / max(1, args.steps + args.warmup))
-    probe = oracle.init(*inputs.turbulence(128, 128, seed=1))
-    t0 = time.perf_counter()
-    oracle.step(probe, p, 2, nthreads=cores)
-    rate = 2 * 128 * 128 / (time.perf_counter() - t0)  # node updates per second
-    n = int((rate * per_step) ** 0.5) // 32 * 32
-    n = max(32, min(1024, n))
-    st = oracle.init(*inputs.turbulence(n, n, seed=1))
     st = oracle.step(st, p, args.warmup, nthreads=cores)
     t0 = time.perf_counter()
     oracle.step(st, p, args.steps, nthreads=cores)
     dt = time.perf_counter() - t0
     value = n * n * args.steps / dt / 1e6
     sample = (f"{n}x{n} lattice of the same turbulence recipe per step (the 8192^2 "
-              f"lattice does not fit the oracle's time budget), FP64 oracle, {cores} threads")
+              f"lattice does not fit the oracle's time budget), FP64 oracle, {cores} threads; "
+              "the same sample as the GPU arm's cpu_baseline")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -190,7 +219,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -706,10 +735,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, s, cores, dtc = time_oracle(budget_s=args.cpu_budget)
-        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"512x512 lattice of the same recipe, {s} FP64 oracle steps "
-                         f"({dtc:.1f} s)"}
+        cpu = time_oracle(budget_s=args.cpu_budget)
 
     traffic = measured_traffic(prec, cells)
 

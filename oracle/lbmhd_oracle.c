@@ -200,22 +200,23 @@ void orc_geq(double ux, double uy, double bx, double by, double* g) {
  * out: the 19 post-collision populations.
  * aux (optional, 4 doubles): tau_nu_eff, tau_m_eff, Q, J.
  */
-static void collide_impl(const double* z, const double* p, const double* shift, double* out,
-                         double* aux);
-static const double* g_taus = NULL; /* les = 3: relaxation times of the node */
+static void collide_impl(const double* z, const double* p, const double* shift,
+                         const double* taus, double* out, double* aux);
 
 void orc_collide_cell(const double* z, const double* p, double* out, double* aux) {
-    collide_impl(z, p, NULL, out, aux);
+    collide_impl(z, p, NULL, NULL, out, aux);
 }
 
 /* As orc_collide_cell, relaxing towards the filtered equilibria shifted by
  * shift = Delta^2 (M3, M4, M7 = M8, N_y1) corrections (les = 2). */
 void orc_collide_cell_shift(const double* z, const double* p, const double* shift, double* out) {
-    collide_impl(z, p, shift, out, NULL);
+    collide_impl(z, p, shift, NULL, out, NULL);
 }
 
-static void collide_impl(const double* z, const double* p, const double* shift, double* out,
-                         double* aux) {
+/* taus (les = 3, else NULL): the node's relaxation times tau_nu, tau_m
+ * from the cross-helicity closure, used instead of the local rates. */
+static void collide_impl(const double* z, const double* p, const double* shift,
+                         const double* taus, double* out, double* aux) {
     setup();
     const double* f = z;
     const double* g = z + NF;
@@ -280,9 +281,9 @@ static void collide_impl(const double* z, const double* p, const double* shift, 
         J = fabs((Ny1 - Ny1eq) - (Nx2 - Nx2eq));
         tau_m = 0.5 * (tau_eta + sqrt(tau_eta * tau_eta + 36.0 * CS * delta * delta * J));
     }
-    if (g_taus) { /* les = 3: rates from the resolved gradients */
-        tau_e = g_taus[0];
-        tau_m = g_taus[1];
+    if (taus) { /* les = 3: rates from the resolved gradients */
+        tau_e = taus[0];
+        tau_m = taus[1];
     }
     double s_nu = 1.0 / tau_e;
     double s[NF];
@@ -371,16 +372,26 @@ static long wrap(long a, long n) {
 static int plane_cx(int p) { return p < NF ? CX[p] : MCX[(p - NF) / 2]; }
 static int plane_cy(int p) { return p < NF ? CY[p] : MCY[(p - NF) / 2]; }
 
-/* Streaming, a pure shift (Sec. 1.2): dst_p(x) = src_p(x - c_p), periodic. */
-void orc_stream(int nx, int ny, const double* src, double* dst) {
+/* Streaming, a pure shift (Sec. 1.2): dst_p(x) = src_p(x - c_p), periodic.
+ * nthreads > 1 splits the rows (OpenMP builds only); each value is a copy,
+ * so the result does not depend on it. */
+static void stream_rows(int nx, int ny, const double* src, double* dst, int nthreads) {
     long N = (long)nx * ny;
+    (void)nthreads;
     for (int p = 0; p < NPLANE; ++p) {
         int cx = plane_cx(p), cy = plane_cy(p);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
         for (long y = 0; y < ny; ++y)
             for (long x = 0; x < nx; ++x)
                 dst[p * N + y * nx + x] =
                     src[p * N + wrap(y - cy, ny) * nx + wrap(x - cx, nx)];
     }
+}
+
+void orc_stream(int nx, int ny, const double* src, double* dst) {
+    stream_rows(nx, ny, src, dst, 1);
 }
 
 /* Equilibrium initialisation: f = f^eq(rho, u, B), g = g^eq(u, B). */
@@ -398,10 +409,11 @@ void orc_init(int nx, int ny, const double* rho, const double* ux, const double*
 
 /* One or more full time steps: stream, then collide at every node.
  * state (19 planes) is advanced in place; work is a caller buffer of the
- * same size.  nthreads > 1 splits the collision loop over rows (OpenMP
- * builds only); results do not depend on it. */
+ * same size.  nthreads > 1 splits the streaming, moment and collision loops
+ * over rows (OpenMP builds only); every node is computed by the same
+ * operations whatever the split, so results do not depend on it. */
 static void kinetic_collide_all(int nx, int ny, const double* p, const double* work,
-                                double* state);
+                                double* state, int nthreads);
 
 int orc_step(int nx, int ny, const double* p, double* state, double* work, int nsteps,
              int nthreads) {
@@ -409,9 +421,9 @@ int orc_step(int nx, int ny, const double* p, double* state, double* work, int n
     long N = (long)nx * ny;
     (void)nthreads;
     for (int t = 0; t < nsteps; ++t) {
-        orc_stream(nx, ny, state, work);
+        stream_rows(nx, ny, state, work, nthreads);
         if (p[P_LES] == 2.0 || p[P_LES] == 3.0) {
-            kinetic_collide_all(nx, ny, p, work, state);
+            kinetic_collide_all(nx, ny, p, work, state, nthreads);
             continue;
         }
 #ifdef _OPENMP
@@ -461,9 +473,13 @@ void orc_carati_taus(const double* p, const double* c0, const double* xp, const 
  * central differences, the filtered-equilibrium shifts, then the collision.
  * les = 3: the same moments give the cross-helicity closure's rates. */
 static void kinetic_collide_all(int nx, int ny, const double* p, const double* work,
-                                double* state) {
+                                double* state, int nthreads) {
     long N = (long)nx * ny;
     double* m = (double*)malloc(sizeof(double) * 5 * N);
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
     for (long c = 0; c < N; ++c) {
         double r = 0, jx = 0, jy = 0, bx = 0, by = 0;
         for (int i = 0; i < NF; ++i) {
@@ -476,6 +492,9 @@ static void kinetic_collide_all(int nx, int ny, const double* p, const double* w
         }
         m[c] = r; m[N + c] = jx; m[2 * N + c] = jy; m[3 * N + c] = bx; m[4 * N + c] = by;
     }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
     for (long y = 0; y < ny; ++y)
         for (long x = 0; x < nx; ++x) {
             long c = y * nx + x;
@@ -490,7 +509,7 @@ static void kinetic_collide_all(int nx, int ny, const double* p, const double* w
             for (int q = 0; q < NPLANE; ++q) z[q] = work[q * N + c];
             if (p[P_LES] == 2.0) {
                 orc_kinetic_shift(fld, grad, p[P_DELTA], sh);
-                collide_impl(z, p, sh, o, NULL);
+                collide_impl(z, p, sh, NULL, o, NULL);
             } else {
                 double a0[5], axp[5], axm[5], ayp[5], aym[5], taus[2];
                 for (int q = 0; q < 5; ++q) {
@@ -499,9 +518,7 @@ static void kinetic_collide_all(int nx, int ny, const double* p, const double* w
                     ayp[q] = m[q * N + yp]; aym[q] = m[q * N + ym];
                 }
                 orc_carati_taus(p, a0, axp, axm, ayp, aym, taus);
-                g_taus = taus;
-                collide_impl(z, p, NULL, o, NULL);
-                g_taus = NULL;
+                collide_impl(z, p, NULL, taus, o, NULL);
             }
             for (int q = 0; q < NPLANE; ++q) state[q * N + c] = o[q];
         }
@@ -542,9 +559,7 @@ void orc_step_cells(int nx, int ny, const double* p, const double* state, long n
             streamed_moments(nx, ny, state, x, y + 1, myp);
             streamed_moments(nx, ny, state, x, y - 1, mym);
             orc_carati_taus(p, m0, mxp, mxm, myp, mym, taus);
-            g_taus = taus;
-            collide_impl(z, p, NULL, out + c * NPLANE, NULL);
-            g_taus = NULL;
+            collide_impl(z, p, NULL, taus, out + c * NPLANE, NULL);
         } else if (p[P_LES] == 2.0) {
             double m0[5], mxp[5], mxm[5], myp[5], mym[5], grad[10], sh[4];
             streamed_moments(nx, ny, state, x, y, m0);
@@ -557,7 +572,7 @@ void orc_step_cells(int nx, int ny, const double* p, const double* state, long n
                 grad[2 * q + 1] = 0.5 * (myp[q] - mym[q]);
             }
             orc_kinetic_shift(m0, grad, p[P_DELTA], sh);
-            collide_impl(z, p, sh, out + c * NPLANE, NULL);
+            collide_impl(z, p, sh, NULL, out + c * NPLANE, NULL);
         } else {
             orc_collide_cell(z, p, out + c * NPLANE, NULL);
         }
