@@ -207,6 +207,46 @@ int lbmhd_set_state_raw(lbmhd_t* h, const void* state, size_t bytes);
  * EINVAL for mismatched handles or rows outside a lattice. */
 int lbmhd_copy_rows(lbmhd_t* dst, int dst_row, lbmhd_t* src, int src_row, int nrows);
 
+/* ---- one step in parts, and halo messages (domain decomposition) --------
+ * The step of Sec. 1.2 / Sec. 3 pulls every population from a neighbour
+ * (streaming is a shift) and collides locally, so a lattice cut into row
+ * slabs can be advanced slab by slab, each slab with ghost rows that hold
+ * copies of its neighbours' boundary rows.  These calls let one handle hold
+ * a slab: the interior rows that need no ghost row are computed while the
+ * halo is in flight, the rows next to the ghosts once it has arrived, and
+ * ghost rows are never computed at all.  (The paper has no counterpart:
+ * this is the sharding of the lattice.)
+ *
+ * lbmhd_step_rows: rows y0 <= y < y1 of the next state (periodic pull) into
+ * the handle's back buffer; the current state is unchanged and stays
+ * current.  Reads rows y0 - 1 .. y1 of the current state (y0 - 2 .. y1 + 1
+ * with les 2, 3, whose moment gradients pull from two rows away).  Rows not
+ * computed before the commit keep the back buffer's older contents.
+ * Asynchronous on the handle's stream; no finite check.  EINVAL unless
+ * 0 <= y0 < y1 <= ny; ESTATE before init.
+ * lbmhd_step_commit: the back buffer becomes the current state and the step
+ * counter advances by one (host only, nothing is enqueued). */
+int lbmhd_step_rows(lbmhd_t* h, int y0, int y1);
+int lbmhd_step_commit(lbmhd_t* h);
+
+/* Halo messages: the planes selected by plane_mask (bit p = plane p of the
+ * 19, in the order f_0..f_8, g_0x, g_0y, ..., g_4y) of row `row` of the
+ * current state, gathered into (pack) or scattered from (unpack) buf: device
+ * memory holding popcount(plane_mask) * nx stored values in the handle's
+ * storage format (lbmhd_get_state_raw's value layout), plane after plane in
+ * increasing plane order, x fastest.  buf is caller-owned, aligned to the
+ * stored value size.  Enqueued on `stream` (cudaStream_t; NULL: the
+ * handle's stream); ordering against the handle's stream is the caller's
+ * (events).  Which planes a ghost row needs: with local rates (les 0, 1)
+ * the ghost row below a slab needs the planes streaming upwards (c_y = +1:
+ * f_2, f_5, f_6, g_2), the one above those streaming downwards; with
+ * les 2, 3 the nearer ghost row also needs the planes with c_y = 0 and the
+ * further one the planes streaming towards the slab.  EINVAL for NULL or
+ * misaligned buf, a row outside the lattice or mask bits above 18; ESTATE
+ * (pack) before init. */
+int lbmhd_pack_row(lbmhd_t* h, int row, unsigned plane_mask, void* buf, void* stream);
+int lbmhd_unpack_row(lbmhd_t* h, int row, unsigned plane_mask, const void* buf, void* stream);
+
 /* Wait for the handle's stream; reports a pending non-finite density. */
 int lbmhd_sync(lbmhd_t* h);
 

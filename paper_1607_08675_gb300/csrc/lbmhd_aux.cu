@@ -614,6 +614,52 @@ cudaError_t launch_set_state(int prec, const double* in, void* state, const Geom
     return cudaGetLastError();
 }
 
+// Halo messages of a decomposed lattice: the selected planes of one row,
+// gathered into (PACK) or scattered from a contiguous buffer, element j of
+// plane slot q at buf[q * nx + j].  W: a stored value's size as an unsigned
+// type of the same width (values are moved, not interpreted).
+struct PlaneList {
+    int p[kPlanes];
+};
+template <class W, bool PACK>
+__global__ void row_planes_kernel(W* __restrict__ state, long long ps, int nx, int row,
+                                  PlaneList pl, int nplanes, W* __restrict__ buf) {
+    const long long n = (long long)nplanes * nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(i / nx);
+        const long long e = pl.p[q] * ps + (long long)row * nx + (i - (long long)q * nx);
+        if (PACK) buf[i] = state[e];
+        else state[e] = buf[i];
+    }
+}
+
+template <class W>
+static cudaError_t row_planes_w(bool pack, void* state, const Geom& g, int row,
+                                const PlaneList& pl, int nplanes, void* buf, cudaStream_t st) {
+    const long long n = (long long)nplanes * g.nx;
+    if (pack)
+        row_planes_kernel<W, true><<<grid_for(n, 256), 256, 0, st>>>((W*)state, g.ps, g.nx, row,
+                                                                     pl, nplanes, (W*)buf);
+    else
+        row_planes_kernel<W, false><<<grid_for(n, 256), 256, 0, st>>>((W*)state, g.ps, g.nx, row,
+                                                                      pl, nplanes, (W*)buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_planes(int prec, bool pack, void* state, const Geom& g, int row,
+                              const int* planes, int nplanes, void* buf, cudaStream_t st) {
+    if (nplanes <= 0) return cudaSuccess;
+    PlaneList pl;
+    for (int q = 0; q < kPlanes; ++q) pl.p[q] = q < nplanes ? planes[q] : 0;
+    switch (storage_bytes(prec)) {
+        case 2: return row_planes_w<unsigned short>(pack, state, g, row, pl, nplanes, buf, st);
+        case 4: return row_planes_w<unsigned int>(pack, state, g, row, pl, nplanes, buf, st);
+        case 8: return row_planes_w<unsigned long long>(pack, state, g, row, pl, nplanes, buf, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_check_finite(int prec, const void* state, int* flag, const Geom& g,
                                 const HostColl& c, cudaStream_t st) {
     const long long n = (long long)g.nx * g.ny;

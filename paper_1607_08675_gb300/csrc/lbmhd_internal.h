@@ -36,9 +36,11 @@ long long plane_stride(int nx, int ny);
 
 // Fused stream-collide step: src -> dst (both 19 planes).  vec = nodes per
 // thread along x (1, 2, 4; nx % vec == 0), block = threads per block,
-// max_blocks = 0 for an exact cover, else a grid-stride cap.
+// max_blocks = 0 for an exact cover, else a grid-stride cap.  Rows
+// [y0, y1) of dst only (y1 < 0: every row); the pull wraps periodically.
 cudaError_t launch_step(int prec, int vec, int block, int max_blocks, const void* src, void* dst,
-                        const Geom& g, const HostColl& c, cudaStream_t st);
+                        const Geom& g, const HostColl& c, cudaStream_t st, int y0 = 0,
+                        int y1 = -1);
 bool step_variant_ok(int prec, int vec, int nx);
 
 // TMA-staged step (lbmhd_step_tma.cu): W threads = nodes per row tile,
@@ -60,9 +62,16 @@ cudaError_t launch_batch_kinetic(int prec, int kin, bool fused, const void* runs
                                  const int* unit_run, unsigned nunits, int block, const void* src,
                                  void* dst, void* mom, float inv_s, cudaStream_t st);
 int kinetic_fused_strip(int prec);
+// Rows [y0, y1) of dst only (y1 < 0: every row); moments are formed for
+// rows y0 - 1 .. y1 (periodic).
 cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
                                 void* dst, void* mom, const Geom& g, const HostColl& c,
-                                cudaStream_t st);
+                                cudaStream_t st, int y0 = 0, int y1 = -1);
+// Gather (pack) or scatter (unpack) the planes planes[0 .. nplanes) of row
+// `row` of a 19-plane state to / from buf, nplanes * nx stored values in
+// plane order (lbmhd_aux.cu).
+cudaError_t launch_row_planes(int prec, bool pack, void* state, const Geom& g, int row,
+                              const int* planes, int nplanes, void* buf, cudaStream_t st);
 cudaError_t launch_step_tma(int prec, int W, int grid, const void* src, void* dst, const Geom& g,
                             const HostColl& c, int* status, cudaStream_t st);
 

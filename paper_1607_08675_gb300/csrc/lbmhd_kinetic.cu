@@ -121,27 +121,33 @@ __device__ __forceinline__ void kin_step_node(const typename Fmt<P>::S* __restri
     for (int q = 0; q < 10; ++q) dst[(9 + q) * ps + node] = Fmt<P>::enc(g[q], 9 + q, 1.0f);
 }
 
+// Moments of the rows ra, ra + 1, ..., ra + nrows - 1 (periodic; ra >= -1).
 template <int P>
 __global__ void __launch_bounds__(256) kin_moments_kernel(const typename Fmt<P>::S* __restrict__ src,
                                                           typename Fmt<P>::R* __restrict__ mom,
                                                           int nx, int ny, long long ps,
-                                                          float inv_s) {
-    const long long n = (long long)nx * ny;
-    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
-         node += (long long)gridDim.x * blockDim.x)
+                                                          float inv_s, int ra, int nrows) {
+    const long long n = (long long)nx * nrows;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / nx);
+        const long long node = (long long)wrapk(ra + r, ny) * nx + (t - (long long)r * nx);
         kin_moments_node<P>(src, mom, nx, ny, ps, node, inv_s);
+    }
 }
 
+// The step of rows y0 .. y0 + nrows - 1.
 template <int P, int MODE>
 __global__ void __launch_bounds__(256) step_kin_kernel(const typename Fmt<P>::S* __restrict__ src,
                                                        typename Fmt<P>::S* __restrict__ dst,
                                                        const typename Fmt<P>::R* __restrict__ mom,
                                                        int nx, int ny, long long ps,
-                                                       Coll<typename Fmt<P>::R> c) {
-    const long long n = (long long)nx * ny;
-    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < n;
-         node += (long long)gridDim.x * blockDim.x)
-        kin_step_node<P, MODE>(src, dst, mom, nx, ny, ps, node, c);
+                                                       Coll<typename Fmt<P>::R> c, int y0,
+                                                       int nrows) {
+    const long long n = (long long)nx * nrows, base = (long long)y0 * nx;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        kin_step_node<P, MODE>(src, dst, mom, nx, ny, ps, base + t, c);
 }
 
 // ---- fused one-pass variant -------------------------------------------------
@@ -306,15 +312,16 @@ __device__ __forceinline__ void kin_fused_body(
     }
 }
 
+// Rows [ya, yb) of the lattice, cut into segments of seglen rows.
 template <int P, int MODE, int SW, int MINB, bool U2>
 __global__ void __launch_bounds__(SW + 32, MINB) step_kin_fused_kernel(
     const typename Fmt<P>::S* __restrict__ src, typename Fmt<P>::S* __restrict__ dst, int nx,
-    int ny, long long ps, int seglen, Coll<typename Fmt<P>::R> c, float inv_s) {
+    int ny, long long ps, int ya, int yb, int seglen, Coll<typename Fmt<P>::R> c, float inv_s) {
     using R = typename Fmt<P>::R;
     __shared__ R ring[kRing][5][SW + 2];
-    const int y0 = blockIdx.y * seglen;
+    const int y0 = ya + blockIdx.y * seglen;
     kin_fused_body<P, MODE, SW, U2>(src, dst, ps, nx, ny, blockIdx.x * SW, y0,
-                                    min(y0 + seglen, ny), c, inv_s, ring);
+                                    min(y0 + seglen, yb), c, inv_s, ring);
 }
 
 // Fused-kernel shape per format: strip width SW (FP64 and FF hold twice the
@@ -340,17 +347,18 @@ inline int fused_seglen(int nx, int ny, int sw, int minb, int sm_count) {
 
 template <int P>
 cudaError_t launch_fused(const void* src, void* dst, const Geom& g, const HostColl& hc,
-                         int sm_count, cudaStream_t st) {
+                         int sm_count, cudaStream_t st, int y0, int y1) {
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
     constexpr int SW = FusedShape<P>::SW, MINB = FusedShape<P>::MINB;
     const int nstrips = (g.nx + SW - 1) / SW;
-    const int seglen = fused_seglen(g.nx, g.ny, SW, MINB, sm_count);
-    const int nseg = (g.ny + seglen - 1) / seglen;
+    const int rows = y1 - y0;
+    const int seglen = fused_seglen(g.nx, rows, SW, MINB, sm_count);
+    const int nseg = (rows + seglen - 1) / seglen;
     const dim3 grid((unsigned)nstrips, (unsigned)nseg);
     auto k = hc.kin == 3 ? step_kin_fused_kernel<P, 3, SW, MINB, false>
                          : step_kin_fused_kernel<P, 2, SW, MINB, true>;
-    k<<<grid, SW + 32, 0, st>>>((const S*)src, (S*)dst, g.nx, g.ny, g.ps, seglen,
+    k<<<grid, SW + 32, 0, st>>>((const S*)src, (S*)dst, g.nx, g.ny, g.ps, y0, y1, seglen,
                                 coll_for_prec<R>(hc, P), hc.inv_scale);
     return cudaGetLastError();
 }
@@ -430,17 +438,23 @@ unsigned kin_grid(long long n) {
 
 template <int P>
 cudaError_t launch_p(const void* src, void* dst, void* mom, const Geom& g, const HostColl& hc,
-                     cudaStream_t st) {
+                     cudaStream_t st, int y0, int y1) {
     auto step = hc.kin == 3 ? step_kin_kernel<P, 3> : step_kin_kernel<P, 2>;
     using S = typename Fmt<P>::S;
     using R = typename Fmt<P>::R;
-    const long long n = (long long)g.nx * g.ny;
-    kin_moments_kernel<P><<<kin_grid(n), 256, 0, st>>>((const S*)src, (R*)mom, g.nx, g.ny, g.ps,
-                                                       hc.inv_scale);
+    // moments of rows y0 - 1 .. y1 (the whole lattice when that covers it)
+    int ra = y0 - 1, mrows = y1 - y0 + 2;
+    if (mrows >= g.ny) {
+        ra = 0;
+        mrows = g.ny;
+    }
+    kin_moments_kernel<P><<<kin_grid((long long)g.nx * mrows), 256, 0, st>>>(
+        (const S*)src, (R*)mom, g.nx, g.ny, g.ps, hc.inv_scale, ra, mrows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    step<<<kin_grid(n), 256, 0, st>>>((const S*)src, (S*)dst, (const R*)mom, g.nx, g.ny, g.ps,
-                                      coll_for_prec<R>(hc, P));
+    step<<<kin_grid((long long)g.nx * (y1 - y0)), 256, 0, st>>>(
+        (const S*)src, (S*)dst, (const R*)mom, g.nx, g.ny, g.ps, coll_for_prec<R>(hc, P), y0,
+        y1 - y0);
     return cudaGetLastError();
 }
 
@@ -477,23 +491,24 @@ int kinetic_fused_strip(int prec) {
 
 cudaError_t launch_step_kinetic(int prec, bool two_pass, int sm_count, const void* src,
                                 void* dst, void* mom, const Geom& g, const HostColl& c,
-                                cudaStream_t st) {
+                                cudaStream_t st, int y0, int y1) {
+    if (y1 < 0) y1 = g.ny;
     if (!two_pass) {
         switch (prec) {
-            case P_FP64: return launch_fused<P_FP64>(src, dst, g, c, sm_count, st);
-            case P_FP32: return launch_fused<P_FP32>(src, dst, g, c, sm_count, st);
-            case P_FP32_DEV: return launch_fused<P_FP32_DEV>(src, dst, g, c, sm_count, st);
-            case P_FP16_DEV: return launch_fused<P_FP16_DEV>(src, dst, g, c, sm_count, st);
-            case P_FF: return launch_fused<P_FF>(src, dst, g, c, sm_count, st);
+            case P_FP64: return launch_fused<P_FP64>(src, dst, g, c, sm_count, st, y0, y1);
+            case P_FP32: return launch_fused<P_FP32>(src, dst, g, c, sm_count, st, y0, y1);
+            case P_FP32_DEV: return launch_fused<P_FP32_DEV>(src, dst, g, c, sm_count, st, y0, y1);
+            case P_FP16_DEV: return launch_fused<P_FP16_DEV>(src, dst, g, c, sm_count, st, y0, y1);
+            case P_FF: return launch_fused<P_FF>(src, dst, g, c, sm_count, st, y0, y1);
         }
         return cudaErrorInvalidValue;
     }
     switch (prec) {
-        case P_FP64: return launch_p<P_FP64>(src, dst, mom, g, c, st);
-        case P_FP32: return launch_p<P_FP32>(src, dst, mom, g, c, st);
-        case P_FP32_DEV: return launch_p<P_FP32_DEV>(src, dst, mom, g, c, st);
-        case P_FP16_DEV: return launch_p<P_FP16_DEV>(src, dst, mom, g, c, st);
-        case P_FF: return launch_p<P_FF>(src, dst, mom, g, c, st);
+        case P_FP64: return launch_p<P_FP64>(src, dst, mom, g, c, st, y0, y1);
+        case P_FP32: return launch_p<P_FP32>(src, dst, mom, g, c, st, y0, y1);
+        case P_FP32_DEV: return launch_p<P_FP32_DEV>(src, dst, mom, g, c, st, y0, y1);
+        case P_FP16_DEV: return launch_p<P_FP16_DEV>(src, dst, mom, g, c, st, y0, y1);
+        case P_FF: return launch_p<P_FF>(src, dst, mom, g, c, st, y0, y1);
     }
     return cudaErrorInvalidValue;
 }

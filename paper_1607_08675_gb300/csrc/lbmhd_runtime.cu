@@ -593,6 +593,67 @@ int lbmhd_copy_rows(lbmhd_t* dst, int dst_row, lbmhd_t* src, int src_row, int nr
     return LBMHD_OK;
 }
 
+int lbmhd_step_rows(lbmhd_t* h, int y0, int y1) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->initialised) return fail(LBMHD_ESTATE, "lbmhd_step_rows before lbmhd_init");
+    if (y0 < 0 || y1 > h->geom.ny || y0 >= y1)
+        return fail(LBMHD_EINVAL, "need 0 <= y0 < y1 <= ny");
+    DeviceGuard dg(h->device);
+    const void* src = h->buf[h->cur];
+    void* dst = h->buf[1 - h->cur];
+    cudaError_t e;
+    if (h->coll.kin)
+        e = launch_step_kinetic(h->p.precision, h->kin_two_pass != 0, h->sm_count, src, dst,
+                                h->d_kin, h->geom, h->coll, h->stream, y0, y1);
+    else
+        e = launch_step(h->p.precision, h->vec, h->block, 0, src, dst, h->geom, h->coll,
+                        h->stream, y0, y1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmhd_step_rows");
+    h->launches += h->coll.kin && h->kin_two_pass ? 2 : 1;
+    return LBMHD_OK;
+}
+
+int lbmhd_step_commit(lbmhd_t* h) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->initialised) return fail(LBMHD_ESTATE, "lbmhd_step_commit before lbmhd_init");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+    return LBMHD_OK;
+}
+
+namespace {
+int row_planes(lbmhd_t* h, bool pack, int row, unsigned mask, void* buf, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!buf) return fail(LBMHD_EINVAL, "buf is NULL");
+    if (row < 0 || row >= h->geom.ny) return fail(LBMHD_EINVAL, "row outside the lattice");
+    if (mask >> kNumPlanes) return fail(LBMHD_EINVAL, "plane_mask has bits above plane 18");
+    if ((uintptr_t)buf % storage_bytes(h->p.precision))
+        return fail(LBMHD_EINVAL, "buf must be aligned to the stored value size");
+    if (pack && !h->initialised) return fail(LBMHD_ESTATE, "lbmhd_pack_row before lbmhd_init");
+    int planes[kNumPlanes], n = 0;
+    for (int p = 0; p < kNumPlanes; ++p)
+        if (mask >> p & 1u) planes[n++] = p;
+    DeviceGuard dg(h->device);
+    const cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    const cudaError_t e =
+        launch_row_planes(h->p.precision, pack, h->buf[h->cur], h->geom, row, planes, n, buf, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, pack ? "lbmhd_pack_row" : "lbmhd_unpack_row");
+    if (!pack) h->initialised = true;
+    return LBMHD_OK;
+}
+}  // namespace
+
+int lbmhd_pack_row(lbmhd_t* h, int row, unsigned plane_mask, void* buf, void* stream) {
+    return row_planes(h, true, row, plane_mask, buf, stream);
+}
+
+int lbmhd_unpack_row(lbmhd_t* h, int row, unsigned plane_mask, const void* buf, void* stream) {
+    return row_planes(h, false, row, plane_mask, const_cast<void*>(buf), stream);
+}
+
 int lbmhd_sync(lbmhd_t* h) {
     int rc = check_handle(h);
     if (rc) return rc;

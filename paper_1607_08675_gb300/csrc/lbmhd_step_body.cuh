@@ -57,15 +57,16 @@ template <int V>
 __device__ __forceinline__ void step_body_h(const unsigned short* __restrict__ src,
                                             unsigned short* __restrict__ dst, int nx, int ny,
                                             long long ps, unsigned t, unsigned total,
-                                            const Coll<float>& c) {
+                                            const Coll<float>& c, int y0) {
     constexpr int W = V / 2;
     using Word = unsigned int;
     const int lane = threadIdx.x & 31;
     const unsigned nxv = (unsigned)(nx / V);
     const bool live = t < total;
     const unsigned tc = live ? t : total - 1;
-    const int y = (int)(tc / nxv);
-    const int x0 = (int)(tc - (unsigned)y * nxv) * V;
+    const unsigned ty = tc / nxv;  // row within the launch
+    const int y = y0 + (int)ty;
+    const int x0 = (int)(tc - ty * nxv) * V;
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
     const bool has_left = lane > 0 && x0 > 0;
@@ -135,15 +136,17 @@ __device__ __forceinline__ void step_body_h(const unsigned short* __restrict__ s
 
 // One thread's step.  All 32 lanes of the warp must call it together
 // (shuffles); t >= total marks a padding thread, which loads valid
-// addresses (those of thread total - 1) and stores nothing.
+// addresses (those of thread total - 1) and stores nothing.  Thread t of a
+// launch over the rows y0 .. y0 + total / (nx / V) - 1 covers row
+// y0 + t / (nx / V).
 template <int P, int V>
 __device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__ src,
                                           typename Fmt<P>::S* __restrict__ dst, int nx, int ny,
                                           long long ps, unsigned t, unsigned total,
                                           const Coll<typename Fmt<P>::R>& c, float scale,
-                                          float inv_scale) {
+                                          float inv_scale, int y0 = 0) {
     if constexpr (P == P_FP16_DEV && V % 2 == 0) {
-        step_body_h<V>(src, dst, nx, ny, ps, t, total, c);
+        step_body_h<V>(src, dst, nx, ny, ps, t, total, c, y0);
         return;
     }
     using S = typename Fmt<P>::S;
@@ -152,8 +155,9 @@ __device__ __forceinline__ void step_body(const typename Fmt<P>::S* __restrict__
     const unsigned nxv = (unsigned)(nx / V);
     const bool live = t < total;
     const unsigned tc = live ? t : total - 1;
-    const int y = (int)(tc / nxv);
-    const int x0 = (int)(tc - (unsigned)y * nxv) * V;
+    const unsigned ty = tc / nxv;  // row within the launch
+    const int y = y0 + (int)ty;
+    const int x0 = (int)(tc - ty * nxv) * V;
     const int ym = y == 0 ? ny - 1 : y - 1;
     const int yp = y == ny - 1 ? 0 : y + 1;
     const bool has_left = lane > 0 && x0 > 0;

@@ -79,6 +79,10 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_set_state_raw": (i, [h, vp, ctypes.c_size_t]),
                 "lbmhd_sync": (i, [h]),
                 "lbmhd_copy_rows": (i, [h, i, h, i, i]),
+                "lbmhd_step_rows": (i, [h, i, i]),
+                "lbmhd_step_commit": (i, [h]),
+                "lbmhd_pack_row": (i, [h, i, ctypes.c_uint, vp, vp]),
+                "lbmhd_unpack_row": (i, [h, i, ctypes.c_uint, vp, vp]),
                 "lbmhd_step_count": (ctypes.c_int64, [h]),
                 "lbmhd_launch_count": (ctypes.c_int64, [h]),
                 "lbmhd_bytes_per_cell": (i, [i]),
@@ -252,6 +256,38 @@ def lbmhd_set_state(h: Handle, state):
 
 def lbmhd_copy_rows(dst: Handle, dst_row: int, src: Handle, src_row: int, nrows: int):
     _check(lib().lbmhd_copy_rows(dst.ptr, int(dst_row), src.ptr, int(src_row), int(nrows)))
+
+
+def lbmhd_step_rows(h: Handle, y0: int, y1: int):
+    _check(lib().lbmhd_step_rows(h.ptr, int(y0), int(y1)))
+
+
+def lbmhd_step_commit(h: Handle):
+    _check(lib().lbmhd_step_commit(h.ptr))
+
+
+def _ptr(x):
+    return x if isinstance(x, int) else x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None or isinstance(stream, int):
+        return ctypes.c_void_p(stream or 0)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def lbmhd_pack_row(h: Handle, row: int, plane_mask: int, buf, stream=None):
+    """Gather the masked planes of one row into ``buf`` (a CUDA tensor or a
+    device address; popcount(plane_mask) * nx stored values)."""
+    _check(lib().lbmhd_pack_row(h.ptr, int(row), ctypes.c_uint(plane_mask),
+                                ctypes.c_void_p(_ptr(buf)), _stream(stream)))
+
+
+def lbmhd_unpack_row(h: Handle, row: int, plane_mask: int, buf, stream=None):
+    """Scatter ``buf`` (as lbmhd_pack_row wrote it) into the masked planes of
+    one row."""
+    _check(lib().lbmhd_unpack_row(h.ptr, int(row), ctypes.c_uint(plane_mask),
+                                  ctypes.c_void_p(_ptr(buf)), _stream(stream)))
 
 
 def lbmhd_sync(h: Handle):
