@@ -275,4 +275,12 @@ def test_step_rows_and_row_planes_through_the_abi(L):
         for row, m, off in ((ny, mask, 0), (-1, mask, 0), (0, 1 << 19, 0), (0, mask, 2)):
             with pytest.raises(L.LBMHDError):
                 L.lbmhd_pack_row(a, row, m, buf.data_ptr() + off)
+        # lbmhd_copy_rows: every plane of a block of rows from one handle to another
+        b = L.lbmhd_create(nx, ny, L.lbmhd_params_default(**kw))
+        L.lbmhd_init(b, *fields)
+        L.lbmhd_copy_rows(b, 2, a, 10, 3)
+        L.lbmhd_sync(b)
+        got = L.lbmhd_get_state_raw(b).view(rawi.dtype).reshape(19, ny, nx)
+        assert np.array_equal(got[:, 2:5], after[:, 10:13])
+        L.lbmhd_destroy(b)
         L.lbmhd_destroy(a)
