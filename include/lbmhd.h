@@ -361,6 +361,55 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
 /* Free the recorded checkpoints (also done by lbmhd_destroy). */
 int lbmhd_adjoint_release(lbmhd_t* h);
 
+/* ---- 3D lattices (D3Q27 density, D3Q7 vector magnetic populations) -------
+ * The paper works in 2D and notes that the model extends to 3D with more
+ * lattice velocities (Sec. 3 opening; the Conclusion names D3Q27).  The 3D
+ * step: D3Q27 populations with the paper's D2Q9 equilibrium written with 3D
+ * vectors plus the 3D trace term -9/2 w |B|^2/6 (zero in 2D), D3Q7 vector
+ * populations with the paper's D2Q5 equilibrium on the six axes (weight
+ * 1/6; the rest weight is zero, so six vector populations are stored), BGK
+ * collision (the paper's MRT with all rates tied) and magnetic SRT, with the
+ * local Smagorinsky rates (les 1) from the traceless non-equilibrium stress
+ * and the axial vector of the magnetic non-equilibrium first moment.
+ * Storage: FP64 or FP32, 45 planes (27 f_i with i = 9 kz + 3 ky + kx,
+ * c = (v[kx], v[ky], v[kz]), v = {0, 1, -1}; then g_q (x, y, z) for
+ * q = +x, -x, +y, -y, +z, -z), node (x, y, z) at (z ny + y) nx + x.  Host
+ * fields: FP64 arrays of nx*ny*nz, x fastest, caller-owned.  Periodic in
+ * x, y and z.  The kinetic closures (les 2, 3) are 2D only. */
+typedef struct lbmhd3_t lbmhd3_t;
+
+/* Uses precision (FP64 or FP32), tau_nu, tau_eta, C_S, delta, les (0, 1)
+ * and stream of p.  Allocates two state buffers.  EINVAL for other
+ * precisions or closures, tau <= 1/2, more than 2^30 nodes; ENOMEM. */
+int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out);
+/* Equilibrium initialisation from seven host fields; synchronises.  EINVAL
+ * for NULL or a density that is not positive and finite. */
+int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
+                const double* uz, const double* bx, const double* by, const double* bz);
+/* n fused stream-collide steps, asynchronous on the handle's stream. */
+int lbmhd3_step(lbmhd3_t* h, int n);
+/* rho, ux, uy, uz, bx, by, bz into out7 (host, 7 * nx*ny*nz doubles, field
+ * after field); synchronises. */
+int lbmhd3_moments(lbmhd3_t* h, double* out7);
+/* The 45 populations as FP64 (host, 45 * nx*ny*nz doubles); synchronises. */
+int lbmhd3_get_state(lbmhd3_t* h, double* out);
+/* FP64 sums, deterministic: mass, momentum (3), sum of B (3), E_K =
+ * <rho |u|^2>/2, E_M = <|B|^2>/2, cross helicity <u.B>, max and rms of the
+ * periodic central-difference div B; synchronises.  The first call
+ * allocates 7 * nx*ny*nz doubles of moment fields kept by the handle. */
+int lbmhd3_diagnostics(lbmhd3_t* h, double* out12);
+/* Work shape: vec nodes per thread along x (1, 2; must divide nx), block
+ * threads (multiple of 32, <= 256).  Results do not depend on it. */
+int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block);
+int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
+int lbmhd3_sync(lbmhd3_t* h);
+int64_t lbmhd3_step_count(const lbmhd3_t* h);
+int64_t lbmhd3_launch_count(const lbmhd3_t* h);
+/* Bytes a 3D step moves per node: 45 values read and written (0 for an
+ * unsupported precision). */
+int lbmhd3_bytes_per_cell(int precision);
+void lbmhd3_destroy(lbmhd3_t* h);
+
 /* ---- ensembles: many independent lattices advanced together ------------
  * A batch holds nruns periodic lattices of their own sizes, each with its
  * own tau_nu, tau_eta and C_S (every other parameter from `common`), and

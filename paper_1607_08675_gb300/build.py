@@ -18,15 +18,16 @@ LIB = os.path.join(HERE, "liblbmhd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["lbmhd_step.cu", "lbmhd_step_tma.cu", "lbmhd_aux.cu", "lbmhd_runtime.cu", "lbmhd_noalloc.cu",
-           "lbmhd_batch.cu", "lbmhd_adjoint.cu", "lbmhd_kinetic.cu"]
+           "lbmhd_batch.cu", "lbmhd_adjoint.cu", "lbmhd_kinetic.cu", "lbmhd3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
-# Per-file flags.  The kinetic-LES kernels are compiled without FMA
-# contraction: the fused and the two-pass kernels perform the same operations
-# in the same order but in differently shaped code, and only with every
-# product rounded on its own is "same operations" also "same bits".
-FILE_FLAGS = {"lbmhd_kinetic.cu": ["-fmad=false"]}
+# Per-file flags.  The kinetic-LES kernels and the 3D step are compiled
+# without FMA contraction: kernels of different shape (fused and two-pass;
+# one or two nodes per thread) perform the same operations in the same order
+# but in differently shaped code, and only with every fusion written out is
+# "same operations" also "same bits".
+FILE_FLAGS = {"lbmhd_kinetic.cu": ["-fmad=false"], "lbmhd3.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

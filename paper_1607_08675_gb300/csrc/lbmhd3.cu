@@ -1,0 +1,719 @@
+// lbmhd3.cu -- the 3D extension of the LB-MHD step (Sec. 3 opening: the
+// model extends to 3D with more lattice velocities; the Conclusion names
+// D3Q27): D3Q27 density populations, D3Q7 vector magnetic populations (the
+// six axes; the rest weight is zero), one fused pull-stream + collide kernel
+// per step, and the handle behind the lbmhd3_* C ABI.
+//
+// Equilibria: the paper's D2Q9 expression with 3D vectors plus the 3D trace
+// term -9/2 w |B|^2/6 (zero in 2D), and the paper's D2Q5 expression on the
+// six axes with w' = 1/6.  Collision: BGK (the paper's MRT with every rate
+// tied), magnetic SRT, with the local Smagorinsky rates of les = 1 from the
+// traceless non-equilibrium stress and the axial vector of the magnetic
+// non-equilibrium first moment.
+//
+// This file is compiled without FMA contraction (-fmad=false) and writes its
+// fused multiply-adds out (fmad), so the one- and two-node launch shapes,
+// whose code the compiler shapes differently, round every operation alike
+// and give the same bits.
+//
+// Layout: 45 SoA planes (27 f_i, then g_q (x, y, z) for q = +x, -x, +y, -y,
+// +z, -z), node (x, y, z) at (z ny + y) nx + x, plane stride padded to 64
+// elements.  f_i with i = 9 kz + 3 ky + kx, c = (v[kx], v[ky], v[kz]),
+// v = {0, 1, -1}.  Arithmetic in deviations d = f - w (g itself).
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbmhd_device.cuh"
+#include "lbmhd_internal.h"
+#include "lbmhd_step_body.cuh"
+
+namespace lbmhd {
+namespace d3 {
+
+constexpr int kQ = 27, kM = 6, kP = kQ + 3 * kM;  // 45 planes
+
+__host__ __device__ constexpr int v1(int k) { return k == 0 ? 0 : (k == 1 ? 1 : -1); }
+// velocity components of plane p (density planes, then the magnetic axes)
+__host__ __device__ constexpr int pcx(int p) {
+    return p < kQ ? v1(p % 3) : ((p - kQ) / 3 == 0 ? 1 : ((p - kQ) / 3 == 1 ? -1 : 0));
+}
+__host__ __device__ constexpr int pcy(int p) {
+    return p < kQ ? v1((p / 3) % 3) : ((p - kQ) / 3 == 2 ? 1 : ((p - kQ) / 3 == 3 ? -1 : 0));
+}
+__host__ __device__ constexpr int pcz(int p) {
+    return p < kQ ? v1(p / 9) : ((p - kQ) / 3 == 4 ? 1 : ((p - kQ) / 3 == 5 ? -1 : 0));
+}
+// D3Q27 weights: the product of the 1D weights {2/3, 1/6, 1/6}
+template <class R>
+__host__ __device__ constexpr R w1(int k) {
+    return k == 0 ? R(2) / R(3) : R(1) / R(6);
+}
+template <class R>
+__host__ __device__ constexpr R wq(int i) {
+    return w1<R>(i % 3) * w1<R>((i / 3) % 3) * w1<R>(i / 9);
+}
+template <class R>
+__host__ __device__ constexpr R plane_rest3(int p) {
+    return p < kQ ? wq<R>(p) : R(0);
+}
+
+template <int P> struct Fmt3;
+template <> struct Fmt3<P_FP64> {
+    using S = double;
+    using R = double;
+    static __device__ __forceinline__ R dec(S v, int p) { return v - plane_rest3<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p) { return d + plane_rest3<R>(p); }
+};
+template <> struct Fmt3<P_FP32> {
+    using S = float;
+    using R = float;
+    static __device__ __forceinline__ R dec(S v, int p) { return v - plane_rest3<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p) { return d + plane_rest3<R>(p); }
+};
+
+template <class R>
+struct Coll3 {
+    R tn, te, tn2, te2, k18, k36;
+    int les;
+};
+
+// One node: d[27] = pulled f_i - w_i, g[18] = pulled g_q (x, y, z);
+// overwritten with the post-collision values.
+template <class R>
+__device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3<R>& c) {
+    // moments: rho - 1, j = rho u, B, and the second moment S = sum d c c
+    R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+    R sxx = R(0), syy = R(0), szz = R(0), sxy = R(0), sxz = R(0), syz = R(0);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int cx = v1(i % 3), cy = v1((i / 3) % 3), cz = v1(i / 9);
+        drho += d[i];
+        if (cx) jx += cx > 0 ? d[i] : -d[i];
+        if (cy) jy += cy > 0 ? d[i] : -d[i];
+        if (cz) jz += cz > 0 ? d[i] : -d[i];
+        if (cx) sxx += d[i];
+        if (cy) syy += d[i];
+        if (cz) szz += d[i];
+        if (cx && cy) sxy += cx * cy > 0 ? d[i] : -d[i];
+        if (cx && cz) sxz += cx * cz > 0 ? d[i] : -d[i];
+        if (cy && cz) syz += cy * cz > 0 ? d[i] : -d[i];
+    }
+    R bx = R(0), by = R(0), bz = R(0);
+#pragma unroll
+    for (int q = 0; q < kM; ++q) {
+        bx += g[3 * q];
+        by += g[3 * q + 1];
+        bz += g[3 * q + 2];
+    }
+    const R rho = R(1) + drho;
+    const R irho = rcp(rho);
+    const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    const R bb = fmad(bz, bz, fmad(by, by, bx * bx));
+    const R jj = fmad(jz, uz, fmad(jy, uy, jx * ux));  // |j|^2 / rho
+
+    // non-equilibrium stress without its isotropic part: S - j j / rho + B B
+    // (the equilibrium's rho/3 I and |B|^2/2 I drop out of the traceless part)
+    R pxx = fmad(bx, bx, fmad(-jx, ux, sxx)), pyy = fmad(by, by, fmad(-jy, uy, syy)),
+      pzz = fmad(bz, bz, fmad(-jz, uz, szz));
+    const R pxy = fmad(bx, by, fmad(-jx, uy, sxy)), pxz = fmad(bx, bz, fmad(-jx, uz, sxz)),
+            pyz = fmad(by, bz, fmad(-jy, uz, syz));
+    const R tr = (pxx + pyy + pzz) * (R(1) / R(3));
+    pxx -= tr;
+    pyy -= tr;
+    pzz -= tr;
+
+    // magnetic non-equilibrium first moment: N_ab = (g_{+a,b} - g_{-a,b})
+    // - (u_a B_b - B_a u_b); its axial vector
+    const R ex = fmad(uy, bz, -(uz * by)), ey = fmad(uz, bx, -(ux * bz)),
+            ez = fmad(ux, by, -(uy * bx));  // u x B
+    const R ax = fmad(R(-2), ex, (g[3 * 2 + 2] - g[3 * 3 + 2]) - (g[3 * 4 + 1] - g[3 * 5 + 1]));
+    const R ay = fmad(R(-2), ey, (g[3 * 4 + 0] - g[3 * 5 + 0]) - (g[3 * 0 + 2] - g[3 * 1 + 2]));
+    const R az = fmad(R(-2), ez, (g[3 * 0 + 1] - g[3 * 1 + 1]) - (g[3 * 2 + 0] - g[3 * 3 + 0]));
+
+    R tau_e = c.tn, tau_m = c.te;
+    if (c.les) {
+        const R off = fmad(pyz, pyz, fmad(pxz, pxz, pxy * pxy));
+        const R pp = fmad(R(2), off, fmad(pzz, pzz, fmad(pyy, pyy, pxx * pxx)));
+        const R Q = sqrt_(R(2) * pp);
+        tau_e = R(0.5) * (c.tn + sqrt_(fmad(c.k18 * Q, irho, c.tn2)));
+        const R J = sqrt_(fmad(az, az, fmad(ay, ay, ax * ax)));
+        tau_m = R(0.5) * (c.te + sqrt_(fmad(c.k36, J, c.te2)));
+    }
+    const R s = rcp(tau_e);
+    // equilibria in deviation form: w [(rho - 1) + 3 c.j + 9/2 (c.j)^2 / rho
+    // - 3/2 j^2 / rho] + 9/2 w [|B|^2/2 |c|^2 - (c.B)^2 - |B|^2/6]
+    const R base = fmad(R(-0.75), bb, fmad(R(-1.5), jj, drho));
+    const R half_bb = R(2.25) * bb;
+    const R k45 = R(4.5) * irho;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int cx = v1(i % 3), cy = v1((i / 3) % 3), cz = v1(i / 9);
+        R cj = R(0), cb = R(0);
+        if (cx) {
+            cj += cx > 0 ? jx : -jx;
+            cb += cx > 0 ? bx : -bx;
+        }
+        if (cy) {
+            cj += cy > 0 ? jy : -jy;
+            cb += cy > 0 ? by : -by;
+        }
+        if (cz) {
+            cj += cz > 0 ? jz : -jz;
+            cb += cz > 0 ? bz : -bz;
+        }
+        const int cc = cx * cx + cy * cy + cz * cz;
+        R t = fmad(R(3), cj, cc ? fmad(half_bb, R(cc), base) : base);
+        t = fmad(k45 * cj, cj, fmad(R(-4.5) * cb, cb, t));
+        const R deq = wq<R>(i) * t;
+        d[i] = fmad(-s, d[i] - deq, d[i]);
+    }
+    // magnetic: g_q^eq = (1/6) [B + 3 ((C.u) B - (C.B) u)]
+    const R sm = rcp(tau_m);
+    const R sixth = R(1) / R(6);
+    const R u3[3] = {ux, uy, uz}, b3[3] = {bx, by, bz};
+#pragma unroll
+    for (int q = 0; q < kM; ++q) {
+        const int a = q / 2;           // axis
+        const R sg3 = q % 2 ? R(-3) : R(3);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b == a) {  // (C.u) B_a - (C.B) u_a = 0 along the axis itself
+                g[3 * q + b] = fmad(-sm, g[3 * q + b] - sixth * b3[b], g[3 * q + b]);
+                continue;
+            }
+            const R e = fmad(u3[a], b3[b], -(b3[a] * u3[b]));
+            const R geq = sixth * fmad(sg3, e, b3[b]);
+            g[3 * q + b] = fmad(-sm, g[3 * q + b] - geq, g[3 * q + b]);
+        }
+    }
+}
+
+struct Geom3 {
+    int nx, ny, nz;
+    long long ps;
+};
+
+// One thread: V consecutive nodes along x of one (y, z) row; every plane one
+// aligned vector load, the x-shifted planes completed from the neighbouring
+// lane by a shuffle (lanes at a warp edge or the periodic wrap load the
+// missing element).  t >= total: a padding thread (valid addresses, no store).
+template <int P, int V>
+__device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict__ src,
+                                           typename Fmt3<P>::S* __restrict__ dst, const Geom3 g,
+                                           unsigned t, unsigned total,
+                                           const Coll3<typename Fmt3<P>::R>& c) {
+    using S = typename Fmt3<P>::S;
+    using R = typename Fmt3<P>::R;
+    const int lane = threadIdx.x & 31;
+    const unsigned nxv = (unsigned)(g.nx / V);
+    const bool live = t < total;
+    const unsigned tc = live ? t : total - 1;
+    const unsigned row = tc / nxv;  // y + ny z
+    const int x0 = (int)(tc - row * nxv) * V;
+    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    const bool has_left = lane > 0 && x0 > 0;
+    const bool has_right = lane < 31 && x0 + V < g.nx;
+    const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;
+    const int xr = x0 + V == g.nx ? 0 : x0 + V;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    S raw[kP][V];
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+        const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
+        const int ry = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const int rz = cz == 0 ? z : (cz > 0 ? zm : zp);
+        const S* base = src + p * g.ps + ((long long)rz * g.ny + ry) * g.nx;
+        const Pack<S, V> pk = *reinterpret_cast<const Pack<S, V>*>(base + x0);
+        if (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) raw[p][k] = pk.v[k];
+        } else if (cx > 0) {
+            S prev = shfl_up1(pk.v[V - 1]);
+            if (!has_left) prev = base[xl];
+            raw[p][0] = prev;
+#pragma unroll
+            for (int k = 1; k < V; ++k) raw[p][k] = pk.v[k - 1];
+        } else {
+            S next = shfl_down1(pk.v[0]);
+            if (!has_right) next = base[xr];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) raw[p][k] = pk.v[k + 1];
+            raw[p][V - 1] = next;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        R d[kQ], gg[3 * kM];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i);
+#pragma unroll
+        for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q);
+        collide3<R>(d, gg, c);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) raw[i][k] = Fmt3<P>::enc(d[i], i);
+#pragma unroll
+        for (int q = 0; q < 3 * kM; ++q) raw[kQ + q][k] = Fmt3<P>::enc(gg[q], kQ + q);
+    }
+    if (live) {
+        const long long node = ((long long)z * g.ny + y) * g.nx + x0;
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            Pack<S, V> o;
+#pragma unroll
+            for (int k = 0; k < V; ++k) o.v[k] = raw[p][k];
+            *reinterpret_cast<Pack<S, V>*>(dst + p * g.ps + node) = o;
+        }
+    }
+}
+
+template <int P, int V>
+__global__ void __launch_bounds__(256) step3_kernel(const typename Fmt3<P>::S* __restrict__ src,
+                                                    typename Fmt3<P>::S* __restrict__ dst,
+                                                    Geom3 g, unsigned total, unsigned total_pad,
+                                                    Coll3<typename Fmt3<P>::R> c) {
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride)
+        step3_body<P, V>(src, dst, g, t, total, c);
+}
+
+// Equilibrium initialisation from seven FP64 device fields.
+template <int P>
+__global__ void init3_kernel(const double* __restrict__ f7, long long n,
+                             typename Fmt3<P>::S* __restrict__ st, long long ps) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double rho = f7[i], u[3] = {f7[n + i], f7[2 * n + i], f7[3 * n + i]},
+                     B[3] = {f7[4 * n + i], f7[5 * n + i], f7[6 * n + i]};
+        const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int p = 0; p < kQ; ++p) {
+            const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
+            const double cu = cx * u[0] + cy * u[1] + cz * u[2];
+            const double cb = cx * B[0] + cy * B[1] + cz * B[2];
+            const double w = wq<double>(p);
+            const double f = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) +
+                             4.5 * w * (0.5 * bb * (cx * cx + cy * cy + cz * cz) - cb * cb - bb / 6.0);
+            st[p * ps + i] = (typename Fmt3<P>::S)f;
+        }
+#pragma unroll
+        for (int q = 0; q < kM; ++q) {
+            const int a = q / 2;
+            const double sg = q % 2 ? -1.0 : 1.0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                st[(kQ + 3 * q + b) * ps + i] = (typename Fmt3<P>::S)(
+                    (B[b] + 3.0 * sg * (u[a] * B[b] - B[a] * u[b])) / 6.0);
+        }
+    }
+}
+
+// rho, u (3), B (3) of the stored state into seven FP64 fields.
+template <int P>
+__global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps,
+                                long long n, double* __restrict__ m7) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int p = 0; p < kQ; ++p) {
+            const double f = (double)st[p * ps + i];
+            rho += f;
+            j[0] += pcx(p) * f;
+            j[1] += pcy(p) * f;
+            j[2] += pcz(p) * f;
+        }
+#pragma unroll
+        for (int q = 0; q < kM; ++q)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) B[b] += (double)st[(kQ + 3 * q + b) * ps + i];
+        m7[i] = rho;
+        for (int a = 0; a < 3; ++a) {
+            m7[(1 + a) * n + i] = j[a] / rho;
+            m7[(4 + a) * n + i] = B[a];
+        }
+    }
+}
+
+// The stored state decoded to 45 FP64 planes of n.
+template <int P>
+__global__ void get3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps, long long n,
+                            double* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int p = 0; p < kP; ++p) out[p * n + i] = (double)st[p * ps + i];
+}
+
+// Diagnostics from the moment fields: per block, FP64 sums in a fixed order
+// (thread sums over a grid-stride range, then a fixed tree), one row of 12
+// per block; a single block then adds the rows in block order.
+constexpr int kDiagBlock3 = 256, kDiagRows3 = 1024;
+__global__ void __launch_bounds__(kDiagBlock3) diag3_kernel(const double* __restrict__ m7,
+                                                            Geom3 g, double* __restrict__ rows) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    double s[12];
+    for (int k = 0; k < 12; ++k) s[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+        const double rho = m7[i];
+        const double u[3] = {m7[n + i], m7[2 * n + i], m7[3 * n + i]};
+        const double B[3] = {m7[4 * n + i], m7[5 * n + i], m7[6 * n + i]};
+        s[0] += rho;
+        for (int a = 0; a < 3; ++a) {
+            s[1 + a] += rho * u[a];
+            s[4 + a] += B[a];
+        }
+        s[7] += 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        s[8] += 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        s[9] += u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+        const long long rowb = ((long long)z * g.ny + y) * g.nx;
+        const long long xp = rowb + (x == g.nx - 1 ? 0 : x + 1), xm = rowb + (x == 0 ? g.nx - 1 : x - 1);
+        const long long yp = ((long long)z * g.ny + (y == g.ny - 1 ? 0 : y + 1)) * g.nx + x;
+        const long long ym = ((long long)z * g.ny + (y == 0 ? g.ny - 1 : y - 1)) * g.nx + x;
+        const long long zp = ((long long)(z == g.nz - 1 ? 0 : z + 1) * g.ny + y) * g.nx + x;
+        const long long zm = ((long long)(z == 0 ? g.nz - 1 : z - 1) * g.ny + y) * g.nx + x;
+        const double div = 0.5 * (m7[4 * n + xp] - m7[4 * n + xm]) + 0.5 * (m7[5 * n + yp] - m7[5 * n + ym]) +
+                           0.5 * (m7[6 * n + zp] - m7[6 * n + zm]);
+        s[10] = fmax(s[10], fabs(div));
+        s[11] += div * div;
+    }
+    __shared__ double red[12][kDiagBlock3];
+    for (int k = 0; k < 12; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kDiagBlock3 / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 12; ++k)
+                red[k][threadIdx.x] = k == 10 ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + w])
+                                              : red[k][threadIdx.x] + red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 12) rows[blockIdx.x * 12 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void diag3_final_kernel(const double* __restrict__ rows, int nrows, long long n,
+                                   double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 12) return;
+    double a = 0.0;
+    for (int r = 0; r < nrows; ++r) a = k == 10 ? fmax(a, rows[r * 12 + k]) : a + rows[r * 12 + k];
+    if (k >= 7 && k <= 9) a /= (double)n;
+    if (k == 11) a = sqrt(a / (double)n);
+    out[k] = a;
+}
+
+unsigned grid3(long long n, int block) {
+    long long b = (n + block - 1) / block;
+    return (unsigned)(b < 1 ? 1 : (b > 65535LL * 64 ? 65535LL * 64 : b));
+}
+
+template <int P, int V>
+cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
+                       const Coll3<typename Fmt3<P>::R>& c, cudaStream_t st) {
+    using S = typename Fmt3<P>::S;
+    const unsigned total = (unsigned)((long long)g.nx / V * g.ny * g.nz);
+    const unsigned total_pad = (total + 31u) / 32u * 32u;
+    step3_kernel<P, V><<<(total_pad + block - 1) / block, block, 0, st>>>((const S*)src, (S*)dst,
+                                                                          g, total, total_pad, c);
+    return cudaGetLastError();
+}
+
+}  // namespace d3
+}  // namespace lbmhd
+
+using namespace lbmhd;
+using namespace lbmhd::d3;
+
+struct lbmhd3_t {
+    Geom3 geom;
+    lbmhd_params p;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    void* buf[2];
+    int cur;
+    bool initialised, failed;
+    int vec, block;
+    int64_t steps, launches;
+    double* d_m7;    // moment fields for the diagnostics (allocated on first use)
+    double* d_rows;  // diagnostics partial rows
+    double* d_out;
+};
+
+namespace {
+
+int fail3(int code, const std::string& m) {
+    set_error(m);
+    return code;
+}
+
+int cuda3(lbmhd3_t* h, cudaError_t e, const char* where) {
+    if (h) h->failed = true;
+    cudaGetLastError();
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return LBMHD_ECUDA;
+}
+
+#define LBMHD3_CK(h, call)                                 \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda3(h, e_, #call); \
+    } while (0)
+
+int check3(lbmhd3_t* h) {
+    if (!h) return fail3(LBMHD_EINVAL, "handle is NULL");
+    if (h->failed) return fail3(LBMHD_ECUDA, "handle is unusable after a CUDA error");
+    return LBMHD_OK;
+}
+
+template <class R>
+Coll3<R> coll3(const lbmhd_params& p) {
+    Coll3<R> c;
+    c.tn = (R)p.tau_nu;
+    c.te = (R)p.tau_eta;
+    c.tn2 = (R)(p.tau_nu * p.tau_nu);
+    c.te2 = (R)(p.tau_eta * p.tau_eta);
+    const double cd2 = p.C_S * p.delta * p.delta;
+    c.k18 = (R)(18.0 * cd2);
+    c.k36 = (R)(36.0 * cd2);
+    c.les = p.les == 1 ? 1 : 0;
+    return c;
+}
+
+long long nodes3(const lbmhd3_t* h) { return (long long)h->geom.nx * h->geom.ny * h->geom.nz; }
+
+cudaError_t one_step3(lbmhd3_t* h) {
+    const void* src = h->buf[h->cur];
+    void* dst = h->buf[1 - h->cur];
+    cudaError_t e = cudaErrorInvalidValue;
+    if (h->p.precision == LBMHD_FP64)
+        e = h->vec == 2 ? launch3_pv<P_FP64, 2>(h->block, src, dst, h->geom, coll3<double>(h->p), h->stream)
+                        : launch3_pv<P_FP64, 1>(h->block, src, dst, h->geom, coll3<double>(h->p), h->stream);
+    else
+        e = h->vec == 2 ? launch3_pv<P_FP32, 2>(h->block, src, dst, h->geom, coll3<float>(h->p), h->stream)
+                        : launch3_pv<P_FP32, 1>(h->block, src, dst, h->geom, coll3<float>(h->p), h->stream);
+    if (e == cudaSuccess) {
+        h->cur = 1 - h->cur;
+        ++h->launches;
+    }
+    return e;
+}
+
+size_t value3_bytes(int prec) { return prec == LBMHD_FP64 ? 8 : (prec == LBMHD_FP32 ? 4 : 0); }
+
+}  // namespace
+
+extern "C" {
+
+int lbmhd3_bytes_per_cell(int precision) { return (int)(2 * kP * value3_bytes(precision)); }
+
+int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out) {
+    if (!out || !p) return fail3(LBMHD_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (p->abi_version != LBMHD_ABI_VERSION) return fail3(LBMHD_EVERSION, "ABI version mismatch");
+    if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 30))
+        return fail3(LBMHD_EINVAL, "nx, ny, nz must be >= 1 with nx*ny*nz <= 2^30 nodes");
+    if (value3_bytes(p->precision) == 0)
+        return fail3(LBMHD_EINVAL, "3D lattices: FP64 or FP32 storage");
+    if (p->les != 0 && p->les != 1)
+        return fail3(LBMHD_EINVAL, "3D lattices: les 0 (off) or 1 (local Smagorinsky rates)");
+    if (!(p->tau_nu > 0.5) || !(p->tau_eta > 0.5) || !(p->tau_nu < 1e6) || !(p->tau_eta < 1e6))
+        return fail3(LBMHD_EINVAL, "tau_nu and tau_eta must be finite and > 1/2");
+    if (!(p->C_S >= 0.0) || !(p->C_S < 1e6) || !(p->delta > 0.0) || !(p->delta < 1e6))
+        return fail3(LBMHD_EINVAL, "C_S must be >= 0 and delta > 0, both finite");
+    lbmhd3_t* h = new (std::nothrow) lbmhd3_t();
+    if (!h) return fail3(LBMHD_ENOMEM, "host allocation failed");
+    std::memset((void*)h, 0, sizeof(*h));
+    h->p = *p;
+    h->geom.nx = nx;
+    h->geom.ny = ny;
+    h->geom.nz = nz;
+    const long long n = (long long)nx * ny * nz;
+    h->geom.ps = (n + 63) / 64 * 64;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda3(nullptr, e, "cudaGetDevice");
+    }
+    if (p->stream) {
+        h->stream = (cudaStream_t)p->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda3(nullptr, e, "cudaStreamCreateWithFlags");
+        }
+        h->own_stream = true;
+    }
+    const size_t bytes = (size_t)kP * h->geom.ps * value3_bytes(p->precision);
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&h->buf[b], bytes);
+        if (e != cudaSuccess) {
+            if (b) cudaFree(h->buf[0]);
+            if (h->own_stream) cudaStreamDestroy(h->stream);
+            delete h;
+            cudaGetLastError();
+            return fail3(e == cudaErrorMemoryAllocation ? LBMHD_ENOMEM : LBMHD_ECUDA,
+                         std::string("device allocation failed: ") + cudaGetErrorString(e));
+        }
+    }
+    // two nodes per thread where nx allows (8- or 16-byte loads), 128 threads
+    h->vec = nx % 2 == 0 ? 2 : 1;
+    h->block = 128;
+    *out = h;
+    return LBMHD_OK;
+}
+
+int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if ((vec != 1 && vec != 2) || h->geom.nx % vec)
+        return fail3(LBMHD_EINVAL, "vec must be 1 or 2 and divide nx");
+    if (block < 32 || block > 256 || block % 32)
+        return fail3(LBMHD_EINVAL, "block must be a multiple of 32 in [32, 256]");
+    h->vec = vec;
+    h->block = block;
+    return LBMHD_OK;
+}
+
+int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block) {
+    if (!h || !vec || !block) return fail3(LBMHD_EINVAL, "NULL argument");
+    *vec = h->vec;
+    *block = h->block;
+    return LBMHD_OK;
+}
+
+int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
+                const double* uz, const double* bx, const double* by, const double* bz) {
+    int rc = check3(h);
+    if (rc) return rc;
+    const double* f[7] = {rho, ux, uy, uz, bx, by, bz};
+    for (int i = 0; i < 7; ++i)
+        if (!f[i]) return fail3(LBMHD_EINVAL, "NULL field");
+    const long long n = nodes3(h);
+    for (long long i = 0; i < n; ++i)
+        if (!(rho[i] > 0.0) || !(rho[i] < 1e300))
+            return fail3(LBMHD_EINVAL, "rho must be positive and finite");
+    double* tmp = nullptr;
+    LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, 7 * n * sizeof(double), h->stream));
+    for (int i = 0; i < 7; ++i)
+        LBMHD3_CK(h, cudaMemcpyAsync(tmp + i * n, f[i], n * sizeof(double), cudaMemcpyHostToDevice,
+                                     h->stream));
+    if (h->p.precision == LBMHD_FP64)
+        init3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>(tmp, n, (double*)h->buf[h->cur], h->geom.ps);
+    else
+        init3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>(tmp, n, (float*)h->buf[h->cur], h->geom.ps);
+    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    h->steps = 0;
+    return LBMHD_OK;
+}
+
+int lbmhd3_step(lbmhd3_t* h, int n) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (n < 0) return fail3(LBMHD_EINVAL, "n must be >= 0");
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "lbmhd3_step before lbmhd3_init");
+    for (int s = 0; s < n; ++s) {
+        LBMHD3_CK(h, one_step3(h));
+        ++h->steps;
+    }
+    return LBMHD_OK;
+}
+
+int lbmhd3_moments(lbmhd3_t* h, double* out7) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!out7) return fail3(LBMHD_EINVAL, "NULL output");
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "moments before lbmhd3_init");
+    const long long n = nodes3(h);
+    double* tmp = nullptr;
+    LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, 7 * n * sizeof(double), h->stream));
+    if (h->p.precision == LBMHD_FP64)
+        moments3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, tmp);
+    else
+        moments3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, tmp);
+    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, cudaMemcpyAsync(out7, tmp, 7 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMHD_OK;
+}
+
+int lbmhd3_get_state(lbmhd3_t* h, double* out) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!out) return fail3(LBMHD_EINVAL, "NULL output");
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "get_state before lbmhd3_init");
+    const long long n = nodes3(h);
+    double* tmp = nullptr;
+    LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, (size_t)kP * n * sizeof(double), h->stream));
+    if (h->p.precision == LBMHD_FP64)
+        get3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, tmp);
+    else
+        get3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, tmp);
+    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, cudaMemcpyAsync(out, tmp, (size_t)kP * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMHD_OK;
+}
+
+int lbmhd3_diagnostics(lbmhd3_t* h, double* out12) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!out12) return fail3(LBMHD_EINVAL, "NULL output");
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "diagnostics before lbmhd3_init");
+    const long long n = nodes3(h);
+    if (!h->d_m7) {
+        LBMHD3_CK(h, cudaMalloc((void**)&h->d_m7, 7 * n * sizeof(double)));
+        LBMHD3_CK(h, cudaMalloc((void**)&h->d_rows, kDiagRows3 * 12 * sizeof(double)));
+        LBMHD3_CK(h, cudaMalloc((void**)&h->d_out, 12 * sizeof(double)));
+    }
+    if (h->p.precision == LBMHD_FP64)
+        moments3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, h->d_m7);
+    else
+        moments3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, h->d_m7);
+    LBMHD3_CK(h, cudaGetLastError());
+    long long nb = (n + kDiagBlock3 - 1) / kDiagBlock3;
+    if (nb > kDiagRows3) nb = kDiagRows3;
+    diag3_kernel<<<(unsigned)nb, kDiagBlock3, 0, h->stream>>>(h->d_m7, h->geom, h->d_rows);
+    LBMHD3_CK(h, cudaGetLastError());
+    diag3_final_kernel<<<1, 32, 0, h->stream>>>(h->d_rows, (int)nb, n, h->d_out);
+    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, cudaMemcpyAsync(out12, h->d_out, 12 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMHD_OK;
+}
+
+int lbmhd3_sync(lbmhd3_t* h) {
+    int rc = check3(h);
+    if (rc) return rc;
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMHD_OK;
+}
+
+int64_t lbmhd3_step_count(const lbmhd3_t* h) { return h ? h->steps : 0; }
+
+int64_t lbmhd3_launch_count(const lbmhd3_t* h) { return h ? h->launches : 0; }
+
+void lbmhd3_destroy(lbmhd3_t* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->d_m7);
+    cudaFree(h->d_rows);
+    cudaFree(h->d_out);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

@@ -14,6 +14,9 @@ with a direct cascade, Sec. 1 and Sec. 3):
     a band of integer wavenumbers, divergence-free by construction.
   * ``ensemble``: a seeded list of independent runs of uneven sizes and
     Smagorinsky constants, for the batched form.
+  * ``turbulence3d``: decaying 3D MHD turbulence for the 3D extension,
+    arrays of shape (nz, ny, nx), u and B discrete curls of band-limited
+    random vector potentials.
 """
 from __future__ import annotations
 
@@ -117,3 +120,42 @@ def ensemble(nruns: int = 256, seed: int = 7, sizes=(128, 256, 512, 1024),
     tau = g.uniform(*tau_range, size=nruns)
     return [dict(nx=int(n[r]), ny=int(n[r]), seed=int(seeds[r]), C_S=float(cs[r]),
                  tau=float(tau[r])) for r in range(nruns)]
+
+
+def _band_field3(nx: int, ny: int, nz: int, kmin: float, kmax: float,
+                 g: np.random.Generator) -> np.ndarray:
+    """A real periodic field of shape (nz, ny, nx) with equal amplitude on
+    every integer wavevector kmin <= |n| <= kmax and random phases."""
+    nzf, nyf, nxf = np.fft.fftfreq(nz) * nz, np.fft.fftfreq(ny) * ny, np.fft.fftfreq(nx) * nx
+    kz, ky, kx = np.meshgrid(nzf, nyf, nxf, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    mask = (kk >= kmin) & (kk <= kmax)
+    spec = np.where(mask, np.exp(2j * np.pi * g.random(kk.shape)), 0.0)
+    return np.real(np.fft.ifftn(spec))
+
+
+def _d3(a: np.ndarray, axis: int) -> np.ndarray:
+    """Periodic central difference along array axis (0 z, 1 y, 2 x)."""
+    return 0.5 * (np.roll(a, -1, axis=axis) - np.roll(a, 1, axis=axis))
+
+
+def curl3(ax: np.ndarray, ay: np.ndarray, az: np.ndarray):
+    """Central-difference curl of a periodic vector field (arrays (nz, ny,
+    nx)); its central-difference divergence is zero."""
+    return (_d3(az, 1) - _d3(ay, 0), _d3(ax, 0) - _d3(az, 2), _d3(ay, 2) - _d3(ax, 1))
+
+
+def turbulence3d(nx: int, ny: int, nz: int, kmin: float = 2.0, kmax: float = 4.0,
+                 rms: float = 0.04, seed: int = 1):
+    """Decaying 3D MHD turbulence: u and B the discrete curls of band-limited
+    random vector potentials, each scaled to sqrt(<|.|^2>) = rms; rho = 1.
+    Returns (rho, ux, uy, uz, bx, by, bz), each (nz, ny, nx)."""
+    g = _rng(seed)
+    out = []
+    for _ in range(2):
+        pot = [_band_field3(nx, ny, nz, kmin, kmax, g) for _ in range(3)]
+        v = curl3(*pot)
+        norm = np.sqrt(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+        out.append([c * (rms / norm) if norm > 0 else c for c in v])
+    rho = np.ones((nz, ny, nx))
+    return (rho, *out[0], *out[1])

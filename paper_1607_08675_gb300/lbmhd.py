@@ -80,6 +80,19 @@ def lib() -> ctypes.CDLL:
                 "lbmhd_sync": (i, [h]),
                 "lbmhd_copy_rows": (i, [h, i, h, i, i]),
                 "lbmhd_step_rows": (i, [h, i, i]),
+                "lbmhd3_create": (i, [i, i, i, ctypes.POINTER(Params), pp]),
+                "lbmhd3_init": (i, [h, vp, vp, vp, vp, vp, vp, vp]),
+                "lbmhd3_step": (i, [h, i]),
+                "lbmhd3_moments": (i, [h, vp]),
+                "lbmhd3_get_state": (i, [h, vp]),
+                "lbmhd3_diagnostics": (i, [h, vp]),
+                "lbmhd3_set_launch": (i, [h, i, i]),
+                "lbmhd3_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i)]),
+                "lbmhd3_sync": (i, [h]),
+                "lbmhd3_step_count": (ctypes.c_int64, [h]),
+                "lbmhd3_launch_count": (ctypes.c_int64, [h]),
+                "lbmhd3_bytes_per_cell": (i, [i]),
+                "lbmhd3_destroy": (None, [h]),
                 "lbmhd_step_commit": (i, [h]),
                 "lbmhd_pack_row": (i, [h, i, ctypes.c_uint, vp, vp]),
                 "lbmhd_unpack_row": (i, [h, i, ctypes.c_uint, vp, vp]),
@@ -357,6 +370,95 @@ def lbmhd_diagnostics_noalloc(state, precision, nx: int, ny: int, plane_stride: 
 def lbmhd_destroy(h: Handle):
     if h is not None and h.ptr:
         lib().lbmhd_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+
+
+# ---- 3D lattices ---------------------------------------------------------
+
+DIAG3_KEYS = ("mass", "mom_x", "mom_y", "mom_z", "bsum_x", "bsum_y", "bsum_z", "E_kin",
+              "E_mag", "cross_helicity", "divB_max", "divB_rms")
+
+
+class Handle3:
+    """An lbmhd3_t* together with its lattice shape (nz, ny, nx)."""
+
+    def __init__(self, ptr: int, nx: int, ny: int, nz: int, params: Params):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.params = params
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def lbmhd3_create(nx: int, ny: int, nz: int, params: Params | None = None) -> Handle3:
+    params = params if params is not None else lbmhd_params_default()
+    out = ctypes.c_void_p()
+    _check(lib().lbmhd3_create(int(nx), int(ny), int(nz), ctypes.byref(params),
+                               ctypes.byref(out)))
+    return Handle3(out.value, nx, ny, nz, params)
+
+
+def lbmhd3_init(h: Handle3, rho, ux, uy, uz, bx, by, bz):
+    arrs = [_host(a, h.shape) for a in (rho, ux, uy, uz, bx, by, bz)]
+    _check(lib().lbmhd3_init(h.ptr, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs]))
+
+
+def lbmhd3_step(h: Handle3, n: int = 1):
+    _check(lib().lbmhd3_step(h.ptr, int(n)))
+
+
+def lbmhd3_moments(h: Handle3):
+    """(rho, ux, uy, uz, bx, by, bz), each (nz, ny, nx)."""
+    out = np.empty((7,) + h.shape)
+    _check(lib().lbmhd3_moments(h.ptr, out.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(out)
+
+
+def lbmhd3_get_state(h: Handle3) -> np.ndarray:
+    st = np.empty((45,) + h.shape)
+    _check(lib().lbmhd3_get_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
+    return st
+
+
+def lbmhd3_diagnostics(h: Handle3) -> dict:
+    out = np.empty(12)
+    _check(lib().lbmhd3_diagnostics(h.ptr, out.ctypes.data_as(ctypes.c_void_p)))
+    return dict(zip(DIAG3_KEYS, out.tolist()))
+
+
+def lbmhd3_set_launch(h: Handle3, vec: int, block: int):
+    _check(lib().lbmhd3_set_launch(h.ptr, int(vec), int(block)))
+
+
+def lbmhd3_get_launch(h: Handle3):
+    v, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbmhd3_get_launch(h.ptr, ctypes.byref(v), ctypes.byref(b)))
+    return v.value, b.value
+
+
+def lbmhd3_sync(h: Handle3):
+    _check(lib().lbmhd3_sync(h.ptr))
+
+
+def lbmhd3_step_count(h: Handle3) -> int:
+    return int(lib().lbmhd3_step_count(h.ptr))
+
+
+def lbmhd3_launch_count(h: Handle3) -> int:
+    return int(lib().lbmhd3_launch_count(h.ptr))
+
+
+def lbmhd3_bytes_per_cell(precision) -> int:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return int(lib().lbmhd3_bytes_per_cell(int(precision)))
+
+
+def lbmhd3_destroy(h: Handle3):
+    if h is not None and h.ptr:
+        lib().lbmhd3_destroy(h.ptr)
         h.ptr = ctypes.c_void_p()
 
 
