@@ -559,12 +559,26 @@ def steps_for(seconds_per_step, min_s=MIN_LEG_S, floor=2):
     return max(floor, int(math.ceil(min_s / max(seconds_per_step, 1e-9))))
 
 
-def timed_leg(L, h, stream, warmup, max_over_ranks_):
+def timed_leg(L, h, stream, warmup, max_over_ranks_, step=None):
     """(steps, seconds) of a leg timed for at least MIN_LEG_S: a 2-step probe
-    after the warm-up sets the step count; max over ranks."""
-    probe = timed_steps(L, h, stream, 2, warmup) / 2
-    steps = steps_for(probe)
-    return steps, max_over_ranks_(timed_steps(L, h, stream, steps, 1))
+    after the warm-up sets the step count; max over ranks.  step: the step
+    call (default lbmhd_step)."""
+    import torch
+
+    step = step or L.lbmhd_step
+
+    def run(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(h, n)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    step(h, warmup)
+    stream.synchronize()
+    steps = steps_for(run(2) / 2)
+    return steps, max_over_ranks_(run(steps))
 
 
 def run_ours(args):
@@ -667,6 +681,26 @@ def run_ours(args):
                 "hbm_frac": vb * cells * vsteps / t / 1e9 / hbm,
             }
 
+    # ---- the 3D extension (D3Q27 + D3Q7 vector), decaying 3D turbulence -----
+    # 45 values read and written per node: 360 B (FP32), 720 B (FP64)
+    variants3d = {}
+    if not args.no_variants:
+        from paper_1607_08675_gb300 import inputs
+
+        for vp, n3 in (("fp32", args.n3), ("fp64", max(16, args.n3 // 2))):
+            h3 = L.lbmhd3_create(n3, n3, n3, L.lbmhd_params_default(
+                precision=vp, tau_nu=0.51, tau_eta=0.51, C_S=0.1, les=1, stream=stream))
+            L.lbmhd3_init(h3, *inputs.turbulence3d(n3, n3, n3, seed=1 + rank))
+            barrier()
+            s3, t = timed_leg(L, h3, stream, 3, max_over_ranks_, step=L.lbmhd3_step)
+            b3 = L.lbmhd3_bytes_per_cell(vp)
+            L.lbmhd3_destroy(h3)
+            variants3d[vp] = {
+                "MLUPS": world * n3 ** 3 * s3 / t / 1e6, "steps": s3, "seconds": t,
+                "lattice": f"{n3}^3", "bytes_per_cell": b3,
+                "hbm_frac": b3 * n3 ** 3 * s3 / t / 1e9 / hbm,
+                "note": "3D decaying turbulence (band 2 <= |n| <= 4, rms 0.04), local LES rates"}
+
     # ---- the FP64 diagnostics reduction on the same lattice ----------------
     # algorithmic bytes: the 19 stored planes, read once (the tiles' halo
     # rows come from L2)
@@ -756,7 +790,8 @@ def run_ours(args):
                          "bytes_per_cell": bpc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "diagnostics": diagnostics,
-            "clocks": clk.summary(), "variants": variants, "batched": batched,
+            "clocks": clk.summary(), "variants": variants, "variants_3d": variants3d,
+            "batched": batched,
             "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
@@ -873,6 +908,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(DTYPES), default="fp32")
     ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--n3", type=int, default=256, help="edge of the 3D lattice legs")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
