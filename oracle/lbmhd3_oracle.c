@@ -35,13 +35,31 @@
  *     N_ab = sum_k C_ka (g_kb - g_kb^eq) (in 2D |N_y1 - N_x2 - 2E|);
  *     tau_e = (tau_nu + sqrt(tau_nu^2 + 18 C_S Delta^2 Q / rho)) / 2,
  *     tau_m = (tau_eta + sqrt(tau_eta^2 + 36 C_S Delta^2 J)) / 2.
+ *   - The paper's kinetic LES (les = 2, Sec. 4.1) in this BGK form: relax
+ *     towards the filtered equilibria f^eq + Delta^2 f^(Delta),
+ *     g^eq + Delta^2 g^(Delta), the corrections obtained by applying the
+ *     product rule P(X, Y) = dX . dY / 12 (Eq. FilterExampleSmall) and the
+ *     ratio rule Rt(X, Y; rho) (Eq. FilterExampleLarge) to every nonlinear
+ *     term of the equilibria: (c.j)^2/rho -> sum_ab c_a c_b Rt(j_a, j_b),
+ *     |j|^2/rho -> sum_a Rt(j_a, j_a), |B|^2 -> sum_a P(B_a, B_a),
+ *     (c.B)^2 -> sum_ab c_a c_b P(B_a, B_b), j_a B_b/rho -> Rt(j_a, B_b).
+ *     The fields are the conserved moments of the streamed populations,
+ *     their gradients periodic central differences (as in 2D).  In 2D these
+ *     are the moment-table corrections the 2D oracle applies (M_3, M_4,
+ *     M_7 = M_8, N_y1); with every rate tied the 2D MRT relaxes towards the
+ *     same shifted distribution.
+ *   - The cross-helicity closure (les = 3, Eqs. CHClosureV/B) with 3D
+ *     vectors: nu_t = C_S Delta^2 |S^v : S^b|^(1/2), eta_t = C_S Delta^2
+ *     sgn(j . omega) |j . omega|^(1/2), omega = curl u, j = curl B, from the
+ *     same central differences of u = j/rho and B; tau_e = tau_nu + 3 nu_t,
+ *     tau_m = max(tau_eta + 3 eta_t, 1/2).
  *
  * State: 45 planes of nx*ny*nz doubles, plane p at offset p*N, node
  * (x, y, z) at (z*ny + y)*nx + x.  Planes 0..26: f_i with i = 9 kz + 3 ky + kx,
  * c = (v[kx], v[ky], v[kz]), v = {0, 1, -1}.  Plane 27 + 3q + a: component a
  * (x, y, z) of g_q, q = 0..5 for C = +x, -x, +y, -y, +z, -z.  The stored
  * state is post-collision; a step pulls from x - c, then collides.
- * Parameter vector p: tau_nu, tau_eta, C_S, Delta, les (0 or 1).
+ * Parameter vector p: tau_nu, tau_eta, C_S, Delta, les (0, 1, 2 or 3).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -109,9 +127,20 @@ void orc3_geq(const double* u, const double* B, double* g) {
     }
 }
 
+static void collide3_impl(const double* z, const double* p, const double* fsh, const double* gsh,
+                          const double* taus, double* out, double* aux);
+
 /* One node: z = the 45 pulled populations; out = post-collision.
  * aux (optional, 4 doubles): tau_e, tau_m, Q, J. */
 void orc3_collide_cell(const double* z, const double* p, double* out, double* aux) {
+    collide3_impl(z, p, NULL, NULL, NULL, out, aux);
+}
+
+/* fsh (27) / gsh (18): Delta^2 corrections of the equilibria (les = 2) or
+ * NULL; taus (2): relaxation times replacing tau_nu, tau_eta (les = 3) or
+ * NULL. */
+static void collide3_impl(const double* z, const double* p, const double* fsh, const double* gsh,
+                          const double* taus, double* out, double* aux) {
     const double* f = z;
     const double* g = z + NQ;
     double tau_nu = p[0], tau_eta = p[1], CS = p[2], delta = p[3];
@@ -130,6 +159,10 @@ void orc3_collide_cell(const double* z, const double* p, double* out, double* au
     double feq[NQ], geq[3 * NM];
     orc3_feq(rho, u, B, feq);
     orc3_geq(u, B, geq);
+    if (fsh)
+        for (int i = 0; i < NQ; ++i) feq[i] += fsh[i];
+    if (gsh)
+        for (int k = 0; k < 3 * NM; ++k) geq[k] += gsh[k];
     /* non-equilibrium stress and its traceless part */
     double P[3][3] = {{0.0}};
     for (int i = 0; i < NQ; ++i) {
@@ -153,7 +186,10 @@ void orc3_collide_cell(const double* z, const double* p, double* out, double* au
     double ax = N[1][2] - N[2][1], ay = N[2][0] - N[0][2], az = N[0][1] - N[1][0];
     double J = sqrt(ax * ax + ay * ay + az * az);
     double tau_e = tau_nu, tau_m = tau_eta;
-    if (les) {
+    if (taus) {
+        tau_e = taus[0];
+        tau_m = taus[1];
+    } else if (les) {
         tau_e = 0.5 * (tau_nu + sqrt(tau_nu * tau_nu + 18.0 * CS * delta * delta * Q / rho));
         tau_m = 0.5 * (tau_eta + sqrt(tau_eta * tau_eta + 36.0 * CS * delta * delta * J));
     }
@@ -165,6 +201,86 @@ void orc3_collide_cell(const double* z, const double* p, double* out, double* au
         aux[2] = Q;
         aux[3] = J;
     }
+}
+
+/* ---- gradient closures (les = 2, 3) --------------------------------------
+ * fld: rho, jx, jy, jz, Bx, By, Bz at the node; grad[3 q + g]: derivative of
+ * field q along axis g (periodic central differences). */
+
+static double dot3(const double* grad, int a, int b) {
+    return grad[3 * a] * grad[3 * b] + grad[3 * a + 1] * grad[3 * b + 1] +
+           grad[3 * a + 2] * grad[3 * b + 2];
+}
+
+/* product rule (Eq. FilterExampleSmall) without the Delta^2 */
+static double pr3(const double* grad, int a, int b) { return dot3(grad, a, b) / 12.0; }
+
+/* ratio rule (Eq. FilterExampleLarge) for X Y / rho, fields a, b */
+static double rt3(const double* fld, const double* grad, int a, int b) {
+    double X = fld[a], Y = fld[b], Z = fld[0];
+    return (dot3(grad, a, b) - (X * dot3(grad, 0, b) + Y * dot3(grad, 0, a) -
+                                X * Y * dot3(grad, 0, 0) / Z) / Z) / (12.0 * Z);
+}
+
+/* Delta^2 corrections of the equilibria (les = 2, see the header). */
+void orc3_kinetic_shift(const double* fld, const double* grad, double delta, double* fsh,
+                        double* gsh) {
+    double d2 = delta * delta;
+    double R[3][3], P[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            R[a][b] = rt3(fld, grad, 1 + a, 1 + b);
+            P[a][b] = pr3(grad, 4 + a, 4 + b);
+        }
+    double trR = R[0][0] + R[1][1] + R[2][2], trP = P[0][0] + P[1][1] + P[2][2];
+    for (int i = 0; i < NQ; ++i) {
+        int c[3];
+        cvec(i, c);
+        double cRc = 0.0, cPc = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                cRc += c[a] * c[b] * R[a][b];
+                cPc += c[a] * c[b] * P[a][b];
+            }
+        double cc = (double)(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        /* the nonlinear terms of orc3_feq, each replaced by its correction */
+        fsh[i] = d2 * wq(i) * (4.5 * cRc - 1.5 * trR + 4.5 * (0.5 * trP * cc - cPc - trP / 6.0));
+    }
+    for (int q = 0; q < NM; ++q) {
+        int a = q / 2;
+        double sg = q % 2 ? -1.0 : 1.0;
+        /* (C.u) B_b - (C.B) u_b = sg (j_a B_b - B_a j_b) / rho */
+        for (int b = 0; b < 3; ++b)
+            gsh[3 * q + b] = d2 * wm(q) * 3.0 * sg *
+                             (rt3(fld, grad, 1 + a, 4 + b) - rt3(fld, grad, 1 + b, 4 + a));
+    }
+}
+
+/* Relaxation times of the cross-helicity closure (les = 3) from the fields
+ * at the six neighbours: f6[6][7] for x+, x-, y+, y-, z+, z-. */
+void orc3_carati_taus(const double* p, const double* f6, double* taus) {
+    double cd2 = p[2] * p[3] * p[3];
+    double gu[3][3], gb[3][3]; /* g[a][c] = d_c v_a */
+    for (int c = 0; c < 3; ++c) {
+        const double* fp = f6 + 7 * (2 * c);
+        const double* fm = f6 + 7 * (2 * c + 1);
+        for (int a = 0; a < 3; ++a) {
+            gu[a][c] = 0.5 * (fp[1 + a] / fp[0] - fm[1 + a] / fm[0]);
+            gb[a][c] = 0.5 * (fp[4 + a] - fm[4 + a]);
+        }
+    }
+    double ss = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            ss += 0.5 * (gu[a][b] + gu[b][a]) * 0.5 * (gb[a][b] + gb[b][a]);
+    double nu_t = cd2 * sqrt(fabs(ss));
+    double om[3] = {gu[2][1] - gu[1][2], gu[0][2] - gu[2][0], gu[1][0] - gu[0][1]};
+    double jc[3] = {gb[2][1] - gb[1][2], gb[0][2] - gb[2][0], gb[1][0] - gb[0][1]};
+    double jw = jc[0] * om[0] + jc[1] * om[1] + jc[2] * om[2];
+    double eta_t = cd2 * (jw > 0.0 ? 1.0 : (jw < 0.0 ? -1.0 : 0.0)) * sqrt(fabs(jw));
+    taus[0] = p[0] + 3.0 * nu_t;
+    taus[1] = p[1] + 3.0 * eta_t;
+    if (taus[1] < 0.5) taus[1] = 0.5;
 }
 
 /* ---- lattice-wide operations --------------------------------------------- */
@@ -216,12 +332,19 @@ void orc3_init(int nx, int ny, int nz, const double* rho, const double* ux, cons
 /* nsteps full steps in place (work: a caller buffer of the same size).
  * nthreads > 1 splits the collision over z planes (OpenMP builds only); the
  * bits do not depend on it. */
+static void kinetic3_collide_all(int nx, int ny, int nz, const double* p, const double* work,
+                                 double* state, int nthreads);
+
 int orc3_step(int nx, int ny, int nz, const double* p, double* state, double* work, int nsteps,
               int nthreads) {
     long N = (long)nx * ny * nz;
     (void)nthreads;
     for (int t = 0; t < nsteps; ++t) {
         orc3_stream(nx, ny, nz, state, work);
+        if (p[4] == 2.0 || p[4] == 3.0) {
+            kinetic3_collide_all(nx, ny, nz, p, work, state, nthreads);
+            continue;
+        }
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
 #endif
@@ -237,22 +360,129 @@ int orc3_step(int nx, int ny, int nz, const double* p, double* state, double* wo
     return 0;
 }
 
+/* rho, j (3), B (3) of the populations streamed into every node (7 planes). */
+static void streamed_fields3(long N, const double* work, double* m) {
+    for (long n = 0; n < N; ++n) {
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < NQ; ++i) {
+            int c[3];
+            cvec(i, c);
+            double fi = work[i * N + n];
+            r += fi;
+            for (int a = 0; a < 3; ++a) j[a] += c[a] * fi;
+        }
+        for (int q = 0; q < NM; ++q)
+            for (int a = 0; a < 3; ++a) B[a] += work[(NQ + 3 * q + a) * N + n];
+        m[n] = r;
+        for (int a = 0; a < 3; ++a) {
+            m[(1 + a) * N + n] = j[a];
+            m[(4 + a) * N + n] = B[a];
+        }
+    }
+}
+
+/* les = 2, 3: the fields of the streamed populations, their central
+ * differences, then the filtered-equilibrium collision or the closure's
+ * relaxation times, node by node. */
+static void kinetic3_collide_all(int nx, int ny, int nz, const double* p, const double* work,
+                                 double* state, int nthreads) {
+    long N = (long)nx * ny * nz;
+    double* m = (double*)malloc(sizeof(double) * 7 * N);
+    (void)nthreads;
+    streamed_fields3(N, work, m);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
+    for (long z = 0; z < nz; ++z)
+        for (long y = 0; y < ny; ++y)
+            for (long x = 0; x < nx; ++x) {
+                long n = (z * ny + y) * nx + x;
+                long nb[6] = {(z * ny + y) * nx + wrap3(x + 1, nx), (z * ny + y) * nx + wrap3(x - 1, nx),
+                              (z * ny + wrap3(y + 1, ny)) * nx + x, (z * ny + wrap3(y - 1, ny)) * nx + x,
+                              (wrap3(z + 1, nz) * ny + y) * nx + x, (wrap3(z - 1, nz) * ny + y) * nx + x};
+                double zz[NP3], o[NP3], fld[7], grad[21];
+                for (int q = 0; q < 7; ++q) {
+                    fld[q] = m[q * N + n];
+                    for (int g = 0; g < 3; ++g)
+                        grad[3 * q + g] = 0.5 * (m[q * N + nb[2 * g]] - m[q * N + nb[2 * g + 1]]);
+                }
+                for (int q = 0; q < NP3; ++q) zz[q] = work[q * N + n];
+                if (p[4] == 2.0) {
+                    double fsh[NQ], gsh[3 * NM];
+                    orc3_kinetic_shift(fld, grad, p[3], fsh, gsh);
+                    collide3_impl(zz, p, fsh, gsh, NULL, o, NULL);
+                } else {
+                    double f6[42], taus[2];
+                    for (int k = 0; k < 6; ++k)
+                        for (int q = 0; q < 7; ++q) f6[7 * k + q] = m[q * N + nb[k]];
+                    orc3_carati_taus(p, f6, taus);
+                    collide3_impl(zz, p, NULL, NULL, taus, o, NULL);
+                }
+                for (int q = 0; q < NP3; ++q) state[q * N + n] = o[q];
+            }
+    free(m);
+}
+
+/* The 45 populations streamed into node (x, y, z) (periodic). */
+static void pulled3(int nx, int ny, int nz, const double* state, long x, long y, long z,
+                    double* zz) {
+    long N = (long)nx * ny * nz;
+    x = wrap3(x, nx);
+    y = wrap3(y, ny);
+    z = wrap3(z, nz);
+    for (int q = 0; q < NP3; ++q) {
+        int cv[3];
+        plane_c(q, cv);
+        zz[q] = state[q * N + (wrap3(z - cv[2], nz) * ny + wrap3(y - cv[1], ny)) * nx +
+                      wrap3(x - cv[0], nx)];
+    }
+}
+
+/* rho, j (3), B (3) of 45 pulled populations. */
+static void fields_of(const double* zz, double* m) {
+    for (int q = 0; q < 7; ++q) m[q] = 0.0;
+    for (int i = 0; i < NQ; ++i) {
+        int c[3];
+        cvec(i, c);
+        m[0] += zz[i];
+        for (int a = 0; a < 3; ++a) m[1 + a] += c[a] * zz[i];
+    }
+    for (int q = 0; q < NM; ++q)
+        for (int a = 0; a < 3; ++a) m[4 + a] += zz[NQ + 3 * q + a];
+}
+
 /* One step at selected nodes only: out[c * 45 + q] = post-collision
  * population q at node idx[c] after streaming from state. */
 void orc3_step_cells(int nx, int ny, int nz, const double* p, const double* state, long ncells,
                      const long* idx, double* out) {
-    long N = (long)nx * ny * nz;
+    static const int NB[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     for (long c = 0; c < ncells; ++c) {
         long n = idx[c];
         long x = n % nx, y = (n / nx) % ny, z = n / ((long)nx * ny);
         double zz[NP3];
-        for (int q = 0; q < NP3; ++q) {
-            int cv[3];
-            plane_c(q, cv);
-            zz[q] = state[q * N + (wrap3(z - cv[2], nz) * ny + wrap3(y - cv[1], ny)) * nx +
-                          wrap3(x - cv[0], nx)];
+        pulled3(nx, ny, nz, state, x, y, z, zz);
+        if (p[4] == 2.0 || p[4] == 3.0) {
+            double f6[42], fld[7], grad[21], nb[NP3];
+            fields_of(zz, fld);
+            for (int k = 0; k < 6; ++k) {
+                pulled3(nx, ny, nz, state, x + NB[k][0], y + NB[k][1], z + NB[k][2], nb);
+                fields_of(nb, f6 + 7 * k);
+            }
+            for (int q = 0; q < 7; ++q)
+                for (int g = 0; g < 3; ++g)
+                    grad[3 * q + g] = 0.5 * (f6[7 * (2 * g) + q] - f6[7 * (2 * g + 1) + q]);
+            if (p[4] == 2.0) {
+                double fsh[NQ], gsh[3 * NM];
+                orc3_kinetic_shift(fld, grad, p[3], fsh, gsh);
+                collide3_impl(zz, p, fsh, gsh, NULL, out + c * NP3, NULL);
+            } else {
+                double taus[2];
+                orc3_carati_taus(p, f6, taus);
+                collide3_impl(zz, p, NULL, NULL, taus, out + c * NP3, NULL);
+            }
+        } else {
+            orc3_collide_cell(zz, p, out + c * NP3, NULL);
         }
-        orc3_collide_cell(zz, p, out + c * NP3, NULL);
     }
 }
 

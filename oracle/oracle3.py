@@ -67,6 +67,8 @@ def _load():
             "orc3_step_cells": (None, [i, i, i, dp, dp, l, lp, dp]),
             "orc3_moments": (None, [i, i, i, dp, dp]),
             "orc3_diagnostics": (None, [i, i, i, dp, dp]),
+            "orc3_kinetic_shift": (None, [dp, dp, d, dp, dp]),
+            "orc3_carati_taus": (None, [dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -82,6 +84,8 @@ def _dp(a: np.ndarray):
 
 
 def params(tau_nu=0.6, tau_eta=0.6, C_S=0.1, delta=1.0, les=1) -> np.ndarray:
+    """les: 0 none, 1 local Smagorinsky rates, 2 the paper's filtered
+    equilibria (kinetic LES), 3 the cross-helicity closure."""
     return np.array([tau_nu, tau_eta, C_S, delta, float(les)], dtype=np.float64)
 
 
@@ -115,6 +119,26 @@ def collide_cell(z: np.ndarray, p: np.ndarray):
     out, aux = np.zeros(NPLANE), np.zeros(4)
     _load().orc3_collide_cell(_dp(z), _dp(p), _dp(out), _dp(aux))
     return out, aux
+
+
+def kinetic_shift(fld, grad, delta):
+    """Delta^2 corrections of the equilibria (les = 2) at one node.
+    fld: rho, jx, jy, jz, Bx, By, Bz; grad (7, 3): d field / d (x, y, z).
+    Returns (f shift (27,), g shift (18,))."""
+    fld = np.ascontiguousarray(fld, np.float64)
+    grad = np.ascontiguousarray(grad, np.float64).reshape(-1)
+    fs, gs = np.zeros(NQ), np.zeros(3 * NM)
+    _load().orc3_kinetic_shift(_dp(fld), _dp(grad), float(delta), _dp(fs), _dp(gs))
+    return fs, gs
+
+
+def carati_taus(p, f6):
+    """(tau_e, tau_m) of the cross-helicity closure from the fields
+    (rho, jx, jy, jz, Bx, By, Bz) at the neighbours x+, x-, y+, y-, z+, z-."""
+    f6 = np.ascontiguousarray(f6, np.float64).reshape(-1)
+    out = np.zeros(2)
+    _load().orc3_carati_taus(_dp(np.ascontiguousarray(p, np.float64)), _dp(f6), _dp(out))
+    return out
 
 
 def init(rho, ux, uy, uz, bx, by, bz) -> np.ndarray:
