@@ -375,12 +375,20 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * c = (v[kx], v[ky], v[kz]), v = {0, 1, -1}; then g_q (x, y, z) for
  * q = +x, -x, +y, -y, +z, -z), node (x, y, z) at (z ny + y) nx + x.  Host
  * fields: FP64 arrays of nx*ny*nz, x fastest, caller-owned.  Periodic in
- * x, y and z.  The kinetic closures (les 2, 3) are 2D only. */
+ * x, y and z.  The gradient closures take two launches per step (a pass
+ * that writes rho - 1, j, B of the streamed populations into seven planes,
+ * then the step with central differences of those planes at the six
+ * neighbours): les 2 relaxes towards the paper's filtered equilibria
+ * (Sec. 4.1; the product and ratio rules of Sec. 2 applied to every
+ * nonlinear term of the 3D equilibria), les 3 takes the cross-helicity
+ * closure's relaxation times (Eqs. CHClosureV/B with 3D strain and curl). */
 typedef struct lbmhd3_t lbmhd3_t;
 
-/* Uses precision (FP64 or FP32), tau_nu, tau_eta, C_S, delta, les (0, 1)
- * and stream of p.  Allocates two state buffers.  EINVAL for other
- * precisions or closures, tau <= 1/2, more than 2^30 nodes; ENOMEM. */
+/* Uses precision (FP64 or FP32), tau_nu, tau_eta, C_S, delta, les (0 off,
+ * 1 local rates, 2 filtered equilibria, 3 cross-helicity closure) and stream
+ * of p.  Allocates two state buffers, and for les 2, 3 seven field planes.
+ * EINVAL for other precisions or closures, tau <= 1/2, more than 2^30
+ * nodes; ENOMEM. */
 int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out);
 /* Equilibrium initialisation from seven host fields; synchronises.  EINVAL
  * for NULL or a density that is not positive and finite. */
@@ -399,7 +407,10 @@ int lbmhd3_get_state(lbmhd3_t* h, double* out);
  * allocates 7 * nx*ny*nz doubles of moment fields kept by the handle. */
 int lbmhd3_diagnostics(lbmhd3_t* h, double* out12);
 /* Work shape: vec nodes per thread along x (1, 2; must divide nx), block
- * threads (multiple of 32, <= 256).  Results do not depend on it. */
+ * threads (multiple of 32, <= 256).  vec 0 (les 2, 3 only; block ignored,
+ * reported as 8): the fused one-pass kernel, in which a CTA sweeps a tile of
+ * 32 x 8 columns along z keeping the fields of consecutive planes in shared
+ * memory; the default for FP32 closures.  Results do not depend on it. */
 int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block);
 int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
 int lbmhd3_sync(lbmhd3_t* h);

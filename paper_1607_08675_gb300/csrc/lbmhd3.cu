@@ -9,7 +9,13 @@
 // six axes with w' = 1/6.  Collision: BGK (the paper's MRT with every rate
 // tied), magnetic SRT, with the local Smagorinsky rates of les = 1 from the
 // traceless non-equilibrium stress and the axial vector of the magnetic
-// non-equilibrium first moment.
+// non-equilibrium first moment.  The two gradient closures take two
+// launches per step: a moments pass (rho - 1, j, B of the populations
+// streamed into every node, seven planes), then the step, which forms
+// central differences of those planes at the six neighbours and either
+// relaxes towards the filtered equilibria (the paper's kinetic LES, Sec. 4.1,
+// les = 2) or takes the cross-helicity closure's relaxation times
+// (Eqs. CHClosureV/B, les = 3).
 //
 // This file is compiled without FMA contraction (-fmad=false) and writes its
 // fused multiply-adds out (fmad), so the one- and two-node launch shapes,
@@ -75,13 +81,24 @@ template <> struct Fmt3<P_FP32> {
 template <class R>
 struct Coll3 {
     R tn, te, tn2, te2, k18, k36;
+    R d12;  // Delta^2 / 12 (les = 2)
+    R cd2;  // C_S Delta^2 (les = 3)
     int les;
 };
 
+// Closure of a step: 0 = none or local rates (les 0, 1), 2 = filtered
+// equilibria, 3 = cross-helicity relaxation times.
+enum { K3_LOCAL = 0, K3_FILTER = 2, K3_CARATI = 3 };
+
 // One node: d[27] = pulled f_i - w_i, g[18] = pulled g_q (x, y, z);
-// overwritten with the post-collision values.
-template <class R>
-__device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3<R>& c) {
+// overwritten with the post-collision values.  MODE K3_FILTER: gr[3 q + a]
+// is the central difference along axis a of field q (rho - 1, j, B) of the
+// streamed populations; MODE K3_CARATI: tau_e3, tau_m3 are the relaxation
+// times.
+template <class R, int MODE = K3_LOCAL>
+__device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3<R>& c,
+                                         const R* gr = nullptr, R tau_e3 = R(0),
+                                         R tau_m3 = R(0)) {
     // moments: rho - 1, j = rho u, B, and the second moment S = sum d c c
     R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
     R sxx = R(0), syy = R(0), szz = R(0), sxy = R(0), sxz = R(0), syz = R(0);
@@ -132,7 +149,11 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
     const R az = fmad(R(-2), ez, (g[3 * 0 + 1] - g[3 * 1 + 1]) - (g[3 * 2 + 0] - g[3 * 3 + 0]));
 
     R tau_e = c.tn, tau_m = c.te;
-    if (c.les) {
+    if constexpr (MODE == K3_CARATI) {
+        tau_e = tau_e3;
+        tau_m = tau_m3;
+    }
+    if (MODE == K3_LOCAL && c.les) {
         const R off = fmad(pyz, pyz, fmad(pxz, pxz, pxy * pxy));
         const R pp = fmad(R(2), off, fmad(pzz, pzz, fmad(pyy, pyy, pxx * pxx)));
         const R Q = sqrt_(R(2) * pp);
@@ -141,6 +162,101 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
         tau_m = R(0.5) * (c.te + sqrt_(fmad(c.k36, J, c.te2)));
     }
     const R s = rcp(tau_e);
+    const R sm = rcp(tau_m);
+    const R sixth = R(1) / R(6);
+    const R u3[3] = {ux, uy, uz}, b3[3] = {bx, by, bz};
+    if constexpr (MODE == K3_FILTER) {
+        const R j3[3] = {jx, jy, jz};
+        // The filter rules of Sec. 2 applied to every nonlinear term of the
+        // equilibria.  With G_a = d j_a - u_a d rho and H_b = d B_b - (B_b /
+        // rho) d rho, the ratio rule (Eq. FilterExampleLarge) is
+        // Rt(X_a, Y_b; rho) = G_a . H_b / (12 rho) and the product rule (Eq.
+        // FilterExampleSmall) P(B_a, B_b) = d B_a . d B_b / 12; times Delta^2:
+        //   (c.j)^2/rho -> c.R.c,  |j|^2/rho -> tr R,  (c.B)^2 -> c.P.c,
+        //   |B|^2 -> tr P,  u_a B_b - B_a u_b -> + Rt(j_a, B_b) - Rt(j_b, B_a).
+        R G[3][3], H[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                G[a][k] = fmad(-u3[a], gr[k], gr[3 * (1 + a) + k]);
+                H[a][k] = fmad(-b3[a] * irho, gr[k], gr[3 * (4 + a) + k]);
+            }
+        const R ci = c.d12 * irho;
+        auto dotGG = [&](int a, int b) { return fmad(G[a][2], G[b][2], fmad(G[a][1], G[b][1], G[a][0] * G[b][0])); };
+        auto dotBB = [&](int a, int b) {
+            const R* A = gr + 3 * (4 + a);
+            const R* B = gr + 3 * (4 + b);
+            return fmad(A[2], B[2], fmad(A[1], B[1], A[0] * B[0]));
+        };
+        auto dotGH = [&](int a, int b) { return fmad(G[a][2], H[b][2], fmad(G[a][1], H[b][1], G[a][0] * H[b][0])); };
+        // Q = j u - B B + Delta^2 (R - P), symmetric; the quadratic form of
+        // the equilibrium's nonlinear part
+        R Rd[3], Pd[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Rd[a] = ci * dotGG(a, a);
+            Pd[a] = c.d12 * dotBB(a, a);
+        }
+        const R trR = Rd[0] + Rd[1] + Rd[2], trP = Pd[0] + Pd[1] + Pd[2];
+        R qd[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qd[a] = fmad(-b3[a], b3[a], fmad(j3[a], u3[a], Rd[a] - Pd[a]));
+        // off-diagonal entries doubled: 2 Q_ab for (xy, xz, yz)
+        R q2[3], em[3];
+        {
+            const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int a = pa[k], b = pb[k];
+                const R t = fmad(ci, dotGG(a, b), fmad(-c.d12, dotBB(a, b), fmad(j3[a], u3[b], -(b3[a] * b3[b]))));
+                q2[k] = R(2) * t;
+                em[k] = fmad(ci, dotGH(a, b) - dotGH(b, a), fmad(u3[a], b3[b], -(b3[a] * u3[b])));
+            }
+        }
+        // sums of the diagonal over the non-zero axes of c
+        const R sxy = qd[0] + qd[1], sxz = qd[0] + qd[2], syz = qd[1] + qd[2], sxyz = sxy + qd[2];
+        const R base = fmad(R(-0.75), bb + trP, fmad(R(-1.5), jj + trR, drho));
+        const R hh = R(2.25) * (bb + trP);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const int cx = v1(i % 3), cy = v1((i / 3) % 3), cz = v1(i / 9);
+            R cj = R(0);
+            if (cx) cj += cx > 0 ? jx : -jx;
+            if (cy) cj += cy > 0 ? jy : -jy;
+            if (cz) cj += cz > 0 ? jz : -jz;
+            const int cc = cx * cx + cy * cy + cz * cz;
+            R qf = R(0);
+            if (cc == 1) qf = cx ? qd[0] : (cy ? qd[1] : qd[2]);
+            if (cc == 2) qf = cz == 0 ? sxy : (cy == 0 ? sxz : syz);
+            if (cc == 3) qf = sxyz;
+            if (cx && cy) qf += cx * cy > 0 ? q2[0] : -q2[0];
+            if (cx && cz) qf += cx * cz > 0 ? q2[1] : -q2[1];
+            if (cy && cz) qf += cy * cz > 0 ? q2[2] : -q2[2];
+            R t = fmad(R(3), cj, cc ? fmad(hh, R(cc), base) : base);
+            t = fmad(R(4.5), qf, t);
+            const R deq = wq<R>(i) * t;
+            d[i] = fmad(-s, d[i] - deq, d[i]);
+        }
+#pragma unroll
+        for (int q = 0; q < kM; ++q) {
+            const int a = q / 2;
+            const R sg3 = q % 2 ? R(-3) : R(3);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) {
+                    g[3 * q + b] = fmad(-sm, g[3 * q + b] - sixth * b3[b], g[3 * q + b]);
+                    continue;
+                }
+                // e(a, b) = -e(b, a); em holds (xy, xz, yz)
+                const int k = a + b - 1;
+                const R e = a < b ? em[k] : -em[k];
+                const R geq = sixth * fmad(sg3, e, b3[b]);
+                g[3 * q + b] = fmad(-sm, g[3 * q + b] - geq, g[3 * q + b]);
+            }
+        }
+        return;
+    }
     // equilibria in deviation form: w [(rho - 1) + 3 c.j + 9/2 (c.j)^2 / rho
     // - 3/2 j^2 / rho] + 9/2 w [|B|^2/2 |c|^2 - (c.B)^2 - |B|^2/6]
     const R base = fmad(R(-0.75), bb, fmad(R(-1.5), jj, drho));
@@ -169,9 +285,6 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
         d[i] = fmad(-s, d[i] - deq, d[i]);
     }
     // magnetic: g_q^eq = (1/6) [B + 3 ((C.u) B - (C.B) u)]
-    const R sm = rcp(tau_m);
-    const R sixth = R(1) / R(6);
-    const R u3[3] = {ux, uy, uz}, b3[3] = {bx, by, bz};
 #pragma unroll
     for (int q = 0; q < kM; ++q) {
         const int a = q / 2;           // axis
@@ -194,31 +307,28 @@ struct Geom3 {
     long long ps;
 };
 
-// One thread: V consecutive nodes along x of one (y, z) row; every plane one
-// aligned vector load, the x-shifted planes completed from the neighbouring
-// lane by a shuffle (lanes at a warp edge or the periodic wrap load the
-// missing element).  t >= total: a padding thread (valid addresses, no store).
+// The pull of one thread: V consecutive nodes along x of one (y, z) row;
+// every plane one aligned vector load, the x-shifted planes completed from
+// the neighbouring lane by a shuffle (lanes at a warp edge or the periodic
+// wrap load the missing element).  tc < total (padding threads pass the
+// last real index, so every address is valid).
 template <int P, int V>
-__device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict__ src,
-                                           typename Fmt3<P>::S* __restrict__ dst, const Geom3 g,
-                                           unsigned t, unsigned total,
-                                           const Coll3<typename Fmt3<P>::R>& c) {
+__device__ __forceinline__ void pull3(const typename Fmt3<P>::S* __restrict__ src, const Geom3 g,
+                                      unsigned tc, typename Fmt3<P>::S (&raw)[kP][V], int& x0,
+                                      int& y, int& z) {
     using S = typename Fmt3<P>::S;
-    using R = typename Fmt3<P>::R;
     const int lane = threadIdx.x & 31;
     const unsigned nxv = (unsigned)(g.nx / V);
-    const bool live = t < total;
-    const unsigned tc = live ? t : total - 1;
     const unsigned row = tc / nxv;  // y + ny z
-    const int x0 = (int)(tc - row * nxv) * V;
-    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    x0 = (int)(tc - row * nxv) * V;
+    y = (int)(row % (unsigned)g.ny);
+    z = (int)(row / (unsigned)g.ny);
     const bool has_left = lane > 0 && x0 > 0;
     const bool has_right = lane < 31 && x0 + V < g.nx;
     const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;
     const int xr = x0 + V == g.nx ? 0 : x0 + V;
     const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-    S raw[kP][V];
 #pragma unroll
     for (int p = 0; p < kP; ++p) {
         const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
@@ -243,6 +353,96 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
             raw[p][V - 1] = next;
         }
     }
+}
+
+// The seven fields rho - 1, j, B of decoded populations, summed in the
+// order collide3 sums them.
+template <class R>
+__device__ __forceinline__ void fields3(const R (&d)[kQ], const R (&g)[3 * kM], R (&m)[7]) {
+    R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int cx = v1(i % 3), cy = v1((i / 3) % 3), cz = v1(i / 9);
+        drho += d[i];
+        if (cx) jx += cx > 0 ? d[i] : -d[i];
+        if (cy) jy += cy > 0 ? d[i] : -d[i];
+        if (cz) jz += cz > 0 ? d[i] : -d[i];
+    }
+    R bx = R(0), by = R(0), bz = R(0);
+#pragma unroll
+    for (int q = 0; q < kM; ++q) {
+        bx += g[3 * q];
+        by += g[3 * q + 1];
+        bz += g[3 * q + 2];
+    }
+    m[0] = drho;
+    m[1] = jx;
+    m[2] = jy;
+    m[3] = jz;
+    m[4] = bx;
+    m[5] = by;
+    m[6] = bz;
+}
+
+// The collision of one node under a gradient closure.  nbv(q, n): field q
+// (rho - 1, jx, jy, jz, Bx, By, Bz of the streamed populations) at
+// neighbour n (x+, x-, y+, y-, z+, z-).
+template <class R, int MODE, class NB>
+__device__ __forceinline__ void closure_collide3(R (&d)[kQ], R (&gg)[3 * kM], const Coll3<R>& c,
+                                                 NB nbv) {
+    if constexpr (MODE == K3_FILTER) {
+        R gr[21];
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gr[3 * q + a] = R(0.5) * (nbv(q, 2 * a) - nbv(q, 2 * a + 1));
+        collide3<R, K3_FILTER>(d, gg, c, gr);
+    } else {
+        // u = j / rho and B at the six neighbours, central differences
+        R gu[3][3], gb[3][3];  // [component][axis]
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R ip = rcp(R(1) + nbv(0, 2 * a)), im = rcp(R(1) + nbv(0, 2 * a + 1));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                gu[b][a] = R(0.5) * fmad(nbv(1 + b, 2 * a), ip, -(nbv(1 + b, 2 * a + 1) * im));
+                gb[b][a] = R(0.5) * (nbv(4 + b, 2 * a) - nbv(4 + b, 2 * a + 1));
+            }
+        }
+        // S^v : S^b with S_ab = (d_b v_a + d_a v_b) / 2
+        R ss = fmad(gu[2][2], gb[2][2], fmad(gu[1][1], gb[1][1], gu[0][0] * gb[0][0]));
+        const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) {
+            const int a = pa[k2], b = pb[k2];
+            ss = fmad(R(0.5) * (gu[a][b] + gu[b][a]), gb[a][b] + gb[b][a], ss);
+        }
+        const R nu_t = c.cd2 * sqrt_(fabs(ss));
+        const R om[3] = {gu[2][1] - gu[1][2], gu[0][2] - gu[2][0], gu[1][0] - gu[0][1]};
+        const R jc[3] = {gb[2][1] - gb[1][2], gb[0][2] - gb[2][0], gb[1][0] - gb[0][1]};
+        const R jw = fmad(jc[2], om[2], fmad(jc[1], om[1], jc[0] * om[0]));
+        const R eta_t = c.cd2 * (jw > R(0) ? R(1) : (jw < R(0) ? R(-1) : R(0))) * sqrt_(fabs(jw));
+        const R te = fmax(fmad(R(3), eta_t, c.te), R(0.5));
+        collide3<R, K3_CARATI>(d, gg, c, nullptr, fmad(R(3), nu_t, c.tn), te);
+    }
+}
+
+// Pull + collide + store of V nodes.  MODE K3_FILTER / K3_CARATI read the
+// seven field planes mom (plane stride g.ps) at the six neighbours of each
+// node.  t >= total: a padding thread (valid addresses, no store).
+template <int P, int V, int MODE>
+__device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict__ src,
+                                           typename Fmt3<P>::S* __restrict__ dst, const Geom3 g,
+                                           unsigned t, unsigned total,
+                                           const Coll3<typename Fmt3<P>::R>& c,
+                                           const typename Fmt3<P>::R* __restrict__ mom) {
+    using S = typename Fmt3<P>::S;
+    using R = typename Fmt3<P>::R;
+    const bool live = t < total;
+    const unsigned tc = live ? t : total - 1;
+    int x0, y, z;
+    S raw[kP][V];
+    pull3<P, V>(src, g, tc, raw, x0, y, z);
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         R d[kQ], gg[3 * kM];
@@ -250,7 +450,20 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
         for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i);
 #pragma unroll
         for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q);
-        collide3<R>(d, gg, c);
+        if constexpr (MODE == K3_LOCAL) {
+            collide3<R>(d, gg, c);
+        } else {
+            const int x = x0 + k;
+            const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+            const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+            const long long row = ((long long)z * g.ny + y) * g.nx;
+            const long long nb[6] = {row + xp, row + xm, ((long long)z * g.ny + yp) * g.nx + x,
+                                     ((long long)z * g.ny + ym) * g.nx + x,
+                                     ((long long)zp * g.ny + y) * g.nx + x,
+                                     ((long long)zm * g.ny + y) * g.nx + x};
+            closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) { return __ldg(mom + q * g.ps + nb[n]); });
+        }
 #pragma unroll
         for (int i = 0; i < kQ; ++i) raw[i][k] = Fmt3<P>::enc(d[i], i);
 #pragma unroll
@@ -268,14 +481,174 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
     }
 }
 
+// The moments pass of the gradient closures: rho - 1, j, B of the
+// populations streamed into every node, into seven planes of R.
 template <int P, int V>
+__global__ void __launch_bounds__(256) mom3_kernel(const typename Fmt3<P>::S* __restrict__ src,
+                                                   typename Fmt3<P>::R* __restrict__ mom, Geom3 g,
+                                                   unsigned total, unsigned total_pad) {
+    using S = typename Fmt3<P>::S;
+    using R = typename Fmt3<P>::R;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride) {
+        const bool live = t < total;
+        int x0, y, z;
+        S raw[kP][V];
+        pull3<P, V>(src, g, live ? t : total - 1, raw, x0, y, z);
+        R m[7][V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            R d[kQ], gg[3 * kM], mk[7];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i);
+#pragma unroll
+            for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q);
+            fields3<R>(d, gg, mk);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) m[q][k] = mk[q];
+        }
+        if (live) {
+            const long long node = ((long long)z * g.ny + y) * g.nx + x0;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                Pack<R, V> o;
+#pragma unroll
+                for (int k = 0; k < V; ++k) o.v[k] = m[q][k];
+                *reinterpret_cast<Pack<R, V>*>(mom + q * g.ps + node) = o;
+            }
+        }
+    }
+}
+
+// ---- fused one-pass form of the gradient closures --------------------------
+// A CTA owns a tile of kFX x kFTY columns (x, y) and a segment [z0, z1) of
+// planes, and sweeps up it.  It keeps the seven fields of the streamed
+// populations of consecutive planes, over the tile and a one-node halo, in
+// a ring of kFRing planes in shared memory.  Per plane z: phase A pulls the
+// populations of plane z + 1 at the tile and halo nodes and writes their
+// fields into the ring; a barrier; phase B pulls plane z again at the tile
+// nodes (the same lines phase A read one plane earlier, from L2), takes the
+// central differences from the ring, collides and stores.  Every stored
+// value is read from DRAM once (halo pulls are neighbouring tiles' lines),
+// so the step moves the 360 B/node of a plain FP32 step instead of the
+// two-pass 416 + 180 B.  Ring of 4 planes: phase A of plane z + 2 may run
+// while a slower thread still reads planes z - 1 .. z + 1 in phase B, and
+// no thread passes the next barrier before every thread has finished that
+// phase B.  Fields, differences and collision are those of the two-pass
+// kernels, so both give the same bits.
+// Measured on GB300, FP32, 256^3, les 2 (MLUPS, fraction of the measured copy
+// bandwidth at 360 B/node): fused 9.6K (0.51); two-pass 8.8K (0.47), each of
+// its passes latency-bound at 0.67-0.73 of copy bandwidth.  ncu at 128^3:
+// the re-pull of phase B misses L2 for ~40% of its lines (DRAM reads 1.47x
+// the stored state), 12 warps per SM (139 registers, 3 CTAs), issue 51%
+// busy; 16-row tiles re-read more (2.1x) and run at 5.9K; an L1 prefetch of
+// the next node's lines and 4-5 CTAs per SM (127 / 96 registers) measured
+// slower.
+constexpr int kFX = 32, kFTY = 8, kFThreads = 128, kFRing = 4;
+
+template <int TY>
+constexpr int fused3_smem_floats() {
+    return kFRing * 7 * (TY + 2) * (kFX + 2);
+}
+
+__device__ __forceinline__ int wrap3i(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// The 45 populations streamed into node (x, y, z), decoded.
+template <int P>
+__device__ __forceinline__ void pull_node3(const typename Fmt3<P>::S* __restrict__ src, const Geom3& g,
+                                           int x, int y, int z, typename Fmt3<P>::R (&d)[kQ],
+                                           typename Fmt3<P>::R (&gg)[3 * kM]) {
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+        const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
+        const int rx = cx == 0 ? x : (cx > 0 ? xm : xp);
+        const int ry = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const int rz = cz == 0 ? z : (cz > 0 ? zm : zp);
+        const unsigned off = ((unsigned)rz * (unsigned)g.ny + (unsigned)ry) * (unsigned)g.nx + (unsigned)rx;
+        const auto v = __ldg(src + p * g.ps + off);
+        if (p < kQ)
+            d[p] = Fmt3<P>::dec(v, p);
+        else
+            gg[p - kQ] = Fmt3<P>::dec(v, p);
+    }
+}
+
+template <int P, int MODE, int TY>
+__global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
+    fused3_kernel(const typename Fmt3<P>::S* __restrict__ src, typename Fmt3<P>::S* __restrict__ dst,
+                  Geom3 g, int tiles_x, int tiles_y, int seglen, Coll3<typename Fmt3<P>::R> c) {
+    using R = typename Fmt3<P>::R;
+    extern __shared__ __align__(16) unsigned char fused3_smem[];
+    R* ring = reinterpret_cast<R*>(fused3_smem);
+    constexpr int HX = kFX + 2, HP = (TY + 2) * HX;  // halo row, halo plane
+    const int tile = (int)blockIdx.x % (tiles_x * tiles_y);
+    const int seg = (int)blockIdx.x / (tiles_x * tiles_y);
+    const int x0 = (tile % tiles_x) * kFX, y0 = (tile / tiles_x) * TY;
+    const int tw = min(kFX, g.nx - x0), th = min(TY, g.ny - y0);
+    const int z0 = seg * seglen, z1 = min(z0 + seglen, g.nz);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int hw = tw + 2, hn = hw * (th + 2);
+
+    // phase A: the fields of plane zz at the tile and halo nodes into its slot
+    auto phase_a = [&](int zz) {
+        const int zw = wrap3i(zz, g.nz);
+        R* slot = ring + (size_t)(((zz % kFRing) + kFRing) % kFRing) * 7 * HP;
+        for (int i = tid; i < hn; i += kFThreads) {
+            const int hy = i / hw, hx = i - hy * hw;
+            const int x = wrap3i(x0 - 1 + hx, g.nx), y = wrap3i(y0 - 1 + hy, g.ny);
+            R d[kQ], gg[3 * kM], m[7];
+            pull_node3<P>(src, g, x, y, zw, d, gg);
+            fields3<R>(d, gg, m);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) slot[q * HP + hy * HX + hx] = m[q];
+        }
+    };
+
+    phase_a(z0 - 1);
+    phase_a(z0);
+    for (int z = z0; z < z1; ++z) {
+        phase_a(z + 1);
+        __syncthreads();
+        const R* sm = ring + (size_t)(((z - 1) % kFRing + kFRing) % kFRing) * 7 * HP;
+        const R* s0 = ring + (size_t)((z % kFRing)) * 7 * HP;
+        const R* sp = ring + (size_t)(((z + 1) % kFRing)) * 7 * HP;
+#pragma unroll 1
+        for (int ly = warp; ly < th; ly += kFThreads / 32) {
+            if (lane >= tw) continue;
+            const int x = x0 + lane, y = y0 + ly;
+            R d[kQ], gg[3 * kM];
+            pull_node3<P>(src, g, x, y, z, d, gg);
+            const int c0 = (ly + 1) * HX + lane + 1;
+            closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) {
+                const int o = q * HP;
+                return n == 0 ? s0[o + c0 + 1]
+                     : n == 1 ? s0[o + c0 - 1]
+                     : n == 2 ? s0[o + c0 + HX]
+                     : n == 3 ? s0[o + c0 - HX]
+                     : n == 4 ? sp[o + c0]
+                              : sm[o + c0];
+            });
+            const unsigned node = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) dst[i * g.ps + node] = Fmt3<P>::enc(d[i], i);
+#pragma unroll
+            for (int q = 0; q < 3 * kM; ++q) dst[(kQ + q) * g.ps + node] = Fmt3<P>::enc(gg[q], kQ + q);
+        }
+    }
+}
+
+template <int P, int V, int MODE>
 __global__ void __launch_bounds__(256) step3_kernel(const typename Fmt3<P>::S* __restrict__ src,
                                                     typename Fmt3<P>::S* __restrict__ dst,
                                                     Geom3 g, unsigned total, unsigned total_pad,
-                                                    Coll3<typename Fmt3<P>::R> c) {
+                                                    Coll3<typename Fmt3<P>::R> c,
+                                                    const typename Fmt3<P>::R* __restrict__ mom) {
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride)
-        step3_body<P, V>(src, dst, g, t, total, c);
+        step3_body<P, V, MODE>(src, dst, g, t, total, c, mom);
 }
 
 // Equilibrium initialisation from seven FP64 device fields.
@@ -410,15 +783,90 @@ unsigned grid3(long long n, int block) {
     return (unsigned)(b < 1 ? 1 : (b > 65535LL * 64 ? 65535LL * 64 : b));
 }
 
+// One step: for les 2, 3 the moments pass into mom, then the step.
 template <int P, int V>
 cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
-                       const Coll3<typename Fmt3<P>::R>& c, cudaStream_t st) {
+                       const Coll3<typename Fmt3<P>::R>& c, int les, void* mom, cudaStream_t st) {
     using S = typename Fmt3<P>::S;
+    using R = typename Fmt3<P>::R;
     const unsigned total = (unsigned)((long long)g.nx / V * g.ny * g.nz);
     const unsigned total_pad = (total + 31u) / 32u * 32u;
-    step3_kernel<P, V><<<(total_pad + block - 1) / block, block, 0, st>>>((const S*)src, (S*)dst,
-                                                                          g, total, total_pad, c);
+    const unsigned blocks = (total_pad + block - 1) / block;
+    if (les == 2 || les == 3) {
+        mom3_kernel<P, V><<<blocks, block, 0, st>>>((const S*)src, (R*)mom, g, total, total_pad);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (les == 2)
+            step3_kernel<P, V, K3_FILTER><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
+                                                                   total_pad, c, (const R*)mom);
+        else
+            step3_kernel<P, V, K3_CARATI><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
+                                                                   total_pad, c, (const R*)mom);
+        return cudaGetLastError();
+    }
+    step3_kernel<P, V, K3_LOCAL><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
+                                                           total_pad, c, nullptr);
     return cudaGetLastError();
+}
+
+// The fused form: tiles x segments work units, one CTA each.  The segment
+// count makes the units fill whole waves of the resident CTAs where it can
+// (each segment also pulls two planes of fields before its first plane).
+template <int P, int MODE, int TY>
+cudaError_t launch_fused3(const void* src, void* dst, const Geom3& g,
+                          const Coll3<typename Fmt3<P>::R>& c, int resident, cudaStream_t st) {
+    using S = typename Fmt3<P>::S;
+    using R = typename Fmt3<P>::R;
+    const int tiles_x = (g.nx + kFX - 1) / kFX, tiles_y = (g.ny + TY - 1) / TY;
+    const long long tiles = (long long)tiles_x * tiles_y;
+    int best_seg = 1;
+    double best = -1.0;
+    for (int waves = 1; waves <= 8; ++waves) {
+        long long nseg = (waves * (long long)resident + tiles / 2) / tiles;
+        if (nseg < 1) nseg = 1;
+        if (nseg > g.nz) nseg = g.nz;
+        const int seglen = (int)((g.nz + nseg - 1) / nseg);
+        nseg = (g.nz + seglen - 1) / seglen;
+        const long long units = tiles * nseg;
+        const long long slots = (units + resident - 1) / resident * resident;
+        const double eff = (double)units / (double)slots * (double)seglen / (seglen + 1.0);
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_seg = seglen;
+        }
+    }
+    const long long units = tiles * ((g.nz + best_seg - 1) / best_seg);
+    if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)fused3_smem_floats<TY>() * sizeof(R);
+    fused3_kernel<P, MODE, TY><<<(unsigned)units, kFThreads, smem, st>>>(
+        (const S*)src, (S*)dst, g, tiles_x, tiles_y, best_seg, c);
+    return cudaGetLastError();
+}
+
+// Opt the fused kernel of one precision and closure in to its shared
+// memory; per_sm: its resident CTAs per SM.
+template <int P, int MODE>
+cudaError_t prepare_fused3_mode(int& per_sm) {
+    using R = typename Fmt3<P>::R;
+    const size_t smem = (size_t)fused3_smem_floats<kFTY>() * sizeof(R);
+    cudaError_t e = cudaFuncSetAttribute(fused3_kernel<P, MODE, kFTY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused3_kernel<P, MODE, kFTY>,
+                                                          kFThreads, smem);
+    return e;
+}
+
+template <int P>
+cudaError_t prepare_fused3(int les, int& per_sm) {
+    return les == 2 ? prepare_fused3_mode<P, K3_FILTER>(per_sm) : prepare_fused3_mode<P, K3_CARATI>(per_sm);
+}
+
+template <int P>
+cudaError_t launch_fused3_p(int les, const void* src, void* dst, const Geom3& g,
+                            const Coll3<typename Fmt3<P>::R>& c, int resident, cudaStream_t st) {
+    return les == 2 ? launch_fused3<P, K3_FILTER, kFTY>(src, dst, g, c, resident, st)
+                    : launch_fused3<P, K3_CARATI, kFTY>(src, dst, g, c, resident, st);
 }
 
 }  // namespace d3
@@ -436,8 +884,10 @@ struct lbmhd3_t {
     void* buf[2];
     int cur;
     bool initialised, failed;
-    int vec, block;
+    int vec, block;      // vec 0: the fused closure kernel (block unused)
+    int fused_resident;  // resident fused CTAs on the device
     int64_t steps, launches;
+    void* mom;       // field planes of the gradient closures (les 2, 3)
     double* d_m7;    // moment fields for the diagnostics (allocated on first use)
     double* d_rows;  // diagnostics partial rows
     double* d_out;
@@ -479,6 +929,8 @@ Coll3<R> coll3(const lbmhd_params& p) {
     const double cd2 = p.C_S * p.delta * p.delta;
     c.k18 = (R)(18.0 * cd2);
     c.k36 = (R)(36.0 * cd2);
+    c.d12 = (R)(p.delta * p.delta / 12.0);
+    c.cd2 = (R)cd2;
     c.les = p.les == 1 ? 1 : 0;
     return c;
 }
@@ -489,15 +941,26 @@ cudaError_t one_step3(lbmhd3_t* h) {
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
     cudaError_t e = cudaErrorInvalidValue;
+    const int les = h->p.les;
+    if (h->vec == 0) {
+        e = h->p.precision == LBMHD_FP64
+                ? launch_fused3_p<P_FP64>(les, src, dst, h->geom, coll3<double>(h->p), h->fused_resident, h->stream)
+                : launch_fused3_p<P_FP32>(les, src, dst, h->geom, coll3<float>(h->p), h->fused_resident, h->stream);
+        if (e == cudaSuccess) {
+            h->cur = 1 - h->cur;
+            ++h->launches;
+        }
+        return e;
+    }
     if (h->p.precision == LBMHD_FP64)
-        e = h->vec == 2 ? launch3_pv<P_FP64, 2>(h->block, src, dst, h->geom, coll3<double>(h->p), h->stream)
-                        : launch3_pv<P_FP64, 1>(h->block, src, dst, h->geom, coll3<double>(h->p), h->stream);
+        e = h->vec == 2 ? launch3_pv<P_FP64, 2>(h->block, src, dst, h->geom, coll3<double>(h->p), les, h->mom, h->stream)
+                        : launch3_pv<P_FP64, 1>(h->block, src, dst, h->geom, coll3<double>(h->p), les, h->mom, h->stream);
     else
-        e = h->vec == 2 ? launch3_pv<P_FP32, 2>(h->block, src, dst, h->geom, coll3<float>(h->p), h->stream)
-                        : launch3_pv<P_FP32, 1>(h->block, src, dst, h->geom, coll3<float>(h->p), h->stream);
+        e = h->vec == 2 ? launch3_pv<P_FP32, 2>(h->block, src, dst, h->geom, coll3<float>(h->p), les, h->mom, h->stream)
+                        : launch3_pv<P_FP32, 1>(h->block, src, dst, h->geom, coll3<float>(h->p), les, h->mom, h->stream);
     if (e == cudaSuccess) {
         h->cur = 1 - h->cur;
-        ++h->launches;
+        h->launches += les >= 2 ? 2 : 1;
     }
     return e;
 }
@@ -518,8 +981,10 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
         return fail3(LBMHD_EINVAL, "nx, ny, nz must be >= 1 with nx*ny*nz <= 2^30 nodes");
     if (value3_bytes(p->precision) == 0)
         return fail3(LBMHD_EINVAL, "3D lattices: FP64 or FP32 storage");
-    if (p->les != 0 && p->les != 1)
-        return fail3(LBMHD_EINVAL, "3D lattices: les 0 (off) or 1 (local Smagorinsky rates)");
+    if (p->les < 0 || p->les > 3)
+        return fail3(LBMHD_EINVAL,
+                     "les must be 0 (off), 1 (local rates), 2 (filtered equilibria) or 3 "
+                     "(cross-helicity closure)");
     if (!(p->tau_nu > 0.5) || !(p->tau_eta > 0.5) || !(p->tau_nu < 1e6) || !(p->tau_eta < 1e6))
         return fail3(LBMHD_EINVAL, "tau_nu and tau_eta must be finite and > 1/2");
     if (!(p->C_S >= 0.0) || !(p->C_S < 1e6) || !(p->delta > 0.0) || !(p->delta < 1e6))
@@ -549,10 +1014,14 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
         h->own_stream = true;
     }
     const size_t bytes = (size_t)kP * h->geom.ps * value3_bytes(p->precision);
-    for (int b = 0; b < 2; ++b) {
-        e = cudaMalloc(&h->buf[b], bytes);
+    const size_t mbytes = p->les >= 2 ? (size_t)7 * h->geom.ps * value3_bytes(p->precision) : 0;
+    void** bufs[3] = {&h->buf[0], &h->buf[1], &h->mom};
+    const size_t sizes[3] = {bytes, bytes, mbytes};
+    for (int b = 0; b < 3; ++b) {
+        if (!sizes[b]) continue;
+        e = cudaMalloc(bufs[b], sizes[b]);
         if (e != cudaSuccess) {
-            if (b) cudaFree(h->buf[0]);
+            for (int k = 0; k < b; ++k) cudaFree(*bufs[k]);
             if (h->own_stream) cudaStreamDestroy(h->stream);
             delete h;
             cudaGetLastError();
@@ -560,9 +1029,28 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
                          std::string("device allocation failed: ") + cudaGetErrorString(e));
         }
     }
-    // two nodes per thread where nx allows (8- or 16-byte loads), 128 threads
-    h->vec = nx % 2 == 0 ? 2 : 1;
+    // two nodes per thread where nx allows (8- or 16-byte loads), 128
+    // threads.  Gradient closures: FP32 takes the fused kernel, FP64 (bound
+    // by its FP64 arithmetic, where the fused kernel measured slower) the
+    // two-pass kernels one node per thread (two nodes need more than 255
+    // registers in FP64).
+    h->vec = nx % 2 == 0 && p->les < 2 ? 2 : 1;
     h->block = 128;
+    if (p->les >= 2 && p->precision == LBMHD_FP32) {  // the fused one-pass kernel
+        h->vec = 0;
+        h->block = kFTY;
+    }
+    if (p->les >= 2) {
+        int per_sm = 0, nsm = 0;
+        e = p->precision == LBMHD_FP64 ? prepare_fused3<P_FP64>(p->les, per_sm)
+                                       : prepare_fused3<P_FP32>(p->les, per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) {
+            lbmhd3_destroy(h);
+            return cuda3(nullptr, e, "fused closure kernel setup");
+        }
+        h->fused_resident = per_sm * nsm > 0 ? per_sm * nsm : 1;
+    }
     *out = h;
     return LBMHD_OK;
 }
@@ -570,8 +1058,14 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
 int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block) {
     int rc = check3(h);
     if (rc) return rc;
+    if (vec == 0) {
+        if (h->p.les < 2) return fail3(LBMHD_EINVAL, "vec 0 (the fused kernel) is for les 2, 3");
+        h->vec = 0;
+        h->block = kFTY;
+        return LBMHD_OK;
+    }
     if ((vec != 1 && vec != 2) || h->geom.nx % vec)
-        return fail3(LBMHD_EINVAL, "vec must be 1 or 2 and divide nx");
+        return fail3(LBMHD_EINVAL, "vec must be 0 (les 2, 3), 1 or 2 and divide nx");
     if (block < 32 || block > 256 || block % 32)
         return fail3(LBMHD_EINVAL, "block must be a multiple of 32 in [32, 256]");
     h->vec = vec;
@@ -709,6 +1203,7 @@ void lbmhd3_destroy(lbmhd3_t* h) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
+    cudaFree(h->mom);
     cudaFree(h->d_m7);
     cudaFree(h->d_rows);
     cudaFree(h->d_out);

@@ -1,7 +1,8 @@
 """The 3D step (D3Q27 + D3Q7) on the GPU against the 3D oracle, through the
 lbmhd3_* C ABI: every population plane and the moments after many steps on
-ragged lattices (FP64 to the 1e-12 bar, FP32 to its storage bar), with and
-without the local LES rates; identical bits across launch shapes; the
+ragged lattices (FP64 to the 1e-12 bar, FP32 to its storage bar), with LES
+off, the local LES rates, the paper's filtered equilibria (kinetic LES) and
+the cross-helicity closure; identical bits across launch shapes; the
 diagnostics; one step at sampled nodes of a larger lattice in the default
 launch shape; the refused configurations."""
 import numpy as np
@@ -67,7 +68,7 @@ def rel_fields(m, ref):
     return out
 
 
-@pytest.mark.parametrize("les", [0, 1])
+@pytest.mark.parametrize("les", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", [(12, 10, 8), (16, 6, 9), (20, 14, 12)])
 def test_fp64_matches_oracle(L, o3, les, shape):
     """Moments relative to their maxima at the 1e-12 bar after 100 steps, on
@@ -84,22 +85,25 @@ def test_fp64_matches_oracle(L, o3, les, shape):
     assert np.max(np.abs(st - ref)) < 1e-14
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 6, 5), (9, 1, 4), (5, 3, 1), (7, 5, 3)])
-def test_fp64_degenerate_shapes(L, o3, shape):
+@pytest.mark.parametrize("les", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 6, 5), (9, 1, 4), (5, 3, 1), (7, 5, 3),
+                                   (2, 2, 2)])
+def test_fp64_degenerate_shapes(L, o3, les, shape):
     """One-node, one-row, one-column and one-plane lattices (every neighbour
-    along a size-1 axis is the node itself) and a small odd lattice: every
-    population to 1e-14 after 25 steps."""
+    along a size-1 axis is the node itself; along a size-2 axis both
+    neighbours are the same node) and a small odd lattice: every population
+    to 1e-14 after 25 steps."""
     nx, ny, nz = shape
     rng = np.random.default_rng(4)
     fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
         0.02 * rng.standard_normal((nz, ny, nx)) for _ in range(6))
-    kw = dict(KW, les=1, precision="fp64")
+    kw = dict(KW, les=les, precision="fp64")
     ref = o3.step(o3.init(*fields), o3.params(**okw(kw)), 25)
     _, st, _ = gpu3(L, fields, 25, **kw)
     assert np.max(np.abs(st - ref)) < 1e-14
 
 
-@pytest.mark.parametrize("les", [0, 1])
+@pytest.mark.parametrize("les", [0, 1, 2, 3])
 def test_fp32_matches_oracle(L, o3, les):
     fields = inputs.turbulence3d(16, 12, 10, kmin=1, kmax=3, rms=0.05, seed=9)
     kw = dict(KW, les=les, precision="fp32")
@@ -110,14 +114,47 @@ def test_fp32_matches_oracle(L, o3, les):
     assert max(e.values()) < 2e-4, e
 
 
-def test_launch_shapes_give_identical_bits(L):
+@pytest.mark.parametrize("les", [1, 2, 3])
+def test_launch_shapes_give_identical_bits(L, les):
     fields = inputs.turbulence3d(32, 8, 6, seed=2)
-    outs = []
+    shapes = ((1, 128), (2, 128), (1, 64), (2, 256))
+    if les >= 2:  # and the fused one-pass kernel
+        shapes += ((0, 8),)
     for prec in ("fp64", "fp32"):
-        sts = [gpu3(L, fields, 30, vec, block, precision=prec, **KW)[1]
-               for vec, block in ((1, 128), (2, 128), (1, 64), (2, 256))]
-        assert all(np.array_equal(sts[0], s) for s in sts[1:]), prec
-        outs.append(sts[0])
+        sts = [gpu3(L, fields, 30, vec, block, precision=prec, **dict(KW, les=les))[1]
+               for vec, block in shapes]
+        assert all(np.array_equal(sts[0], s) for s in sts[1:]), (prec, les)
+
+
+@pytest.mark.parametrize("les", [2, 3])
+@pytest.mark.parametrize("shape", [(33, 17, 5), (70, 9, 3), (5, 3, 1), (1, 1, 1), (2, 2, 2),
+                                   (40, 40, 40)])
+def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
+    """Ragged tiles (x not a multiple of 32, y not of 8), planes fewer than
+    the ring, one-node and size-2 axes, and a lattice of many segments: the
+    fused kernel's bits are the two-pass kernel's."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + ny + nz)
+    fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
+        0.02 * rng.standard_normal((nz, ny, nx)) for _ in range(6))
+    for prec in ("fp32", "fp64"):
+        kw = dict(KW, les=les, precision=prec)
+        ref = gpu3(L, fields, 12, 1, 128, **kw)[1]
+        got = gpu3(L, fields, 12, 0, 8, **kw)[1]
+        assert np.array_equal(got, ref), prec
+
+
+@pytest.mark.parametrize("les", [2, 3])
+def test_gradient_closure_launches_per_step(L, les):
+    """Two launches per step in the two-pass form, one in the fused form."""
+    fields = inputs.turbulence3d(8, 6, 4, seed=3)
+    for vec, per_step in ((1, 2), (0, 1)):
+        h = L.lbmhd3_create(8, 6, 4, L.lbmhd_params_default(precision="fp32", les=les, **KW))
+        L.lbmhd3_set_launch(h, vec, 128)
+        L.lbmhd3_init(h, *fields)
+        L.lbmhd3_step(h, 5)
+        assert L.lbmhd3_launch_count(h) == 5 * per_step and L.lbmhd3_step_count(h) == 5
+        L.lbmhd3_destroy(h)
 
 
 def test_diagnostics_match_oracle(L, o3):
@@ -134,13 +171,14 @@ def test_diagnostics_match_oracle(L, o3):
         assert abs(d[k] - v) <= tol, (k, d[k], v)
 
 
-def test_sampled_step_of_a_larger_lattice(L, o3):
+@pytest.mark.parametrize("les", [1, 2, 3])
+def test_sampled_step_of_a_larger_lattice(L, o3, les):
     """128 x 96 x 64 (786,432 nodes, the default launch shape), FP32: one
     step from a developed state, 3,000 sampled nodes against the oracle's
     step of the same stored state (decoded exactly)."""
     nx, ny, nz = 128, 96, 64
     fields = inputs.turbulence3d(nx, ny, nz, seed=11)
-    kw = dict(KW, les=1, precision="fp32")
+    kw = dict(KW, les=les, precision="fp32")
     h = L.lbmhd3_create(nx, ny, nz, L.lbmhd_params_default(**kw))
     L.lbmhd3_init(h, *fields)
     L.lbmhd3_step(h, 10)
@@ -156,7 +194,7 @@ def test_sampled_step_of_a_larger_lattice(L, o3):
 
 
 def test_refused_configurations(L):
-    for bad in (dict(les=2), dict(les=3), dict(precision="fp16_dev"), dict(precision="ff"),
+    for bad in (dict(les=4), dict(les=-1), dict(precision="fp16_dev"), dict(precision="ff"),
                 dict(tau_nu=0.5)):
         with pytest.raises(L.LBMHDError) as e:
             L.lbmhd3_create(8, 8, 8, L.lbmhd_params_default(**dict(dict(precision="fp32"), **bad)))
@@ -166,4 +204,9 @@ def test_refused_configurations(L):
         L.lbmhd3_step(h, 1)  # before init
     with pytest.raises(L.LBMHDError):
         L.lbmhd3_set_launch(h, 4, 128)
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd3_set_launch(h, 0, 8)  # the fused kernel is for les 2, 3
+    L.lbmhd3_destroy(h)
+    h = L.lbmhd3_create(6, 4, 4, L.lbmhd_params_default(precision="fp32", les=2))
+    assert L.lbmhd3_get_launch(h) == (0, 8)  # FP32 closures default to the fused kernel
     L.lbmhd3_destroy(h)
