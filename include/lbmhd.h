@@ -408,9 +408,10 @@ int lbmhd3_get_state(lbmhd3_t* h, double* out);
 int lbmhd3_diagnostics(lbmhd3_t* h, double* out12);
 /* Work shape: vec nodes per thread along x (1, 2; must divide nx), block
  * threads (multiple of 32, <= 256).  vec 0 (les 2, 3 only; block ignored,
- * reported as 8): the fused one-pass kernel, in which a CTA sweeps a tile of
- * 32 x 8 columns along z keeping the fields of consecutive planes in shared
- * memory; the default for FP32 closures.  Results do not depend on it. */
+ * reported as 4): the fused one-pass kernel, in which a CTA sweeps a tile of
+ * 32 x 4 columns along z keeping the fields of consecutive planes and the
+ * tile's pulled values in shared memory; the default for FP32 closures.
+ * Results do not depend on it. */
 int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block);
 int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
 int lbmhd3_sync(lbmhd3_t* h);

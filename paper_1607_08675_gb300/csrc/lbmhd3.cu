@@ -522,34 +522,33 @@ __global__ void __launch_bounds__(256) mom3_kernel(const typename Fmt3<P>::S* __
 
 // ---- fused one-pass form of the gradient closures --------------------------
 // A CTA owns a tile of kFX x kFTY columns (x, y) and a segment [z0, z1) of
-// planes, and sweeps up it.  It keeps the seven fields of the streamed
-// populations of consecutive planes, over the tile and a one-node halo, in
-// a ring of kFRing planes in shared memory.  Per plane z: phase A pulls the
-// populations of plane z + 1 at the tile and halo nodes and writes their
-// fields into the ring; a barrier; phase B pulls plane z again at the tile
-// nodes (the same lines phase A read one plane earlier, from L2), takes the
-// central differences from the ring, collides and stores.  Every stored
-// value is read from DRAM once (halo pulls are neighbouring tiles' lines),
-// so the step moves the 360 B/node of a plain FP32 step instead of the
-// two-pass 416 + 180 B.  Ring of 4 planes: phase A of plane z + 2 may run
-// while a slower thread still reads planes z - 1 .. z + 1 in phase B, and
-// no thread passes the next barrier before every thread has finished that
-// phase B.  Fields, differences and collision are those of the two-pass
-// kernels, so both give the same bits.
+// planes, and sweeps up it.  Shared memory holds the seven fields of the
+// streamed populations of three consecutive planes over the tile and a
+// one-node halo (a ring), and the 45 pulled values of the tile's nodes for
+// two planes.  Per plane z: phase A pulls the populations of plane z + 1 at
+// the tile and halo nodes, writes their fields into the ring and keeps the
+// tile nodes' values; a barrier; phase B takes the values of plane z kept
+// one plane earlier, the central differences from the ring, collides and
+// stores; a barrier.  Every stored value is read once per step by phase A
+// (halo pulls are neighbouring tiles' lines, from L2), so the step moves
+// the 360 B/node of a plain FP32 step instead of the two-pass 416 + 180 B.
+// The two barriers let phase A of plane z + 2 overwrite the ring slot of
+// plane z - 1 and the kept values of plane z only after every thread has
+// finished phase B of plane z.  Fields, differences and collision are those
+// of the two-pass kernels, so both give the same bits.
 // Measured on GB300, FP32, 256^3, les 2 (MLUPS, fraction of the measured copy
-// bandwidth at 360 B/node): fused 9.6K (0.51); two-pass 8.8K (0.47), each of
-// its passes latency-bound at 0.67-0.73 of copy bandwidth.  ncu at 128^3:
-// the re-pull of phase B misses L2 for ~40% of its lines (DRAM reads 1.47x
-// the stored state), 12 warps per SM (139 registers, 3 CTAs), issue 51%
-// busy; 16-row tiles re-read more (2.1x) and run at 5.9K; an L1 prefetch of
-// the next node's lines and 4-5 CTAs per SM (127 / 96 registers) measured
-// slower.
-constexpr int kFX = 32, kFTY = 8, kFThreads = 128, kFRing = 4;
+// bandwidth at 360 B/node): 10.2K (0.54); the two-pass kernels 8.8K (0.47),
+// each of its passes latency-bound at 0.67-0.73 of copy bandwidth.  Earlier
+// forms, measured slower: phase B pulling plane z again from L2 instead of
+// keeping it (8-row tiles, 9.6K: ncu at 128^3 shows that re-pull missing L2
+// for ~40% of its lines, DRAM reads 1.47x the stored state, 12 warps per SM
+// at 139 registers, issue 51% busy; 16-row tiles 5.9K, re-reads 2.1x), an
+// L1 prefetch of the next node's lines (8.0K), 4 and 5 CTAs per SM at 127
+// and 96 registers (9.5K, 8.8K), 8-row tiles with kept values (one CTA per
+// SM, 7.0K).  What remains is latency in phase A at 12 warps per SM.
+constexpr int kFX = 32, kFTY = 4, kFThreads = 128, kFRing = 3;
 
-template <int TY>
-constexpr int fused3_smem_floats() {
-    return kFRing * 7 * (TY + 2) * (kFX + 2);
-}
+constexpr int fused3_smem_floats() { return kFRing * 7 * (kFTY + 2) * (kFX + 2) + 2 * kP * kFTY * kFX; }
 
 __device__ __forceinline__ int wrap3i(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -576,26 +575,30 @@ __device__ __forceinline__ void pull_node3(const typename Fmt3<P>::S* __restrict
     }
 }
 
-template <int P, int MODE, int TY>
+template <int P, int MODE>
 __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
     fused3_kernel(const typename Fmt3<P>::S* __restrict__ src, typename Fmt3<P>::S* __restrict__ dst,
                   Geom3 g, int tiles_x, int tiles_y, int seglen, Coll3<typename Fmt3<P>::R> c) {
     using R = typename Fmt3<P>::R;
     extern __shared__ __align__(16) unsigned char fused3_smem[];
+    constexpr int HX = kFX + 2, HP = (kFTY + 2) * HX;  // halo row, halo plane
+    constexpr int KP = kFTY * kFX;                     // one kept plane of a population
     R* ring = reinterpret_cast<R*>(fused3_smem);
-    constexpr int HX = kFX + 2, HP = (TY + 2) * HX;  // halo row, halo plane
+    R* kept = ring + kFRing * 7 * HP;
     const int tile = (int)blockIdx.x % (tiles_x * tiles_y);
     const int seg = (int)blockIdx.x / (tiles_x * tiles_y);
-    const int x0 = (tile % tiles_x) * kFX, y0 = (tile / tiles_x) * TY;
-    const int tw = min(kFX, g.nx - x0), th = min(TY, g.ny - y0);
+    const int x0 = (tile % tiles_x) * kFX, y0 = (tile / tiles_x) * kFTY;
+    const int tw = min(kFX, g.nx - x0), th = min(kFTY, g.ny - y0);
     const int z0 = seg * seglen, z1 = min(z0 + seglen, g.nz);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int hw = tw + 2, hn = hw * (th + 2);
 
-    // phase A: the fields of plane zz at the tile and halo nodes into its slot
+    // phase A: the fields of plane zz at the tile and halo nodes into its ring
+    // slot, the tile nodes' pulled values into kept buffer zz mod 2
     auto phase_a = [&](int zz) {
         const int zw = wrap3i(zz, g.nz);
         R* slot = ring + (size_t)(((zz % kFRing) + kFRing) % kFRing) * 7 * HP;
+        R* kz = kept + (size_t)(zz & 1) * kP * KP;
         for (int i = tid; i < hn; i += kFThreads) {
             const int hy = i / hw, hx = i - hy * hw;
             const int x = wrap3i(x0 - 1 + hx, g.nx), y = wrap3i(y0 - 1 + hy, g.ny);
@@ -604,6 +607,13 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
             fields3<R>(d, gg, m);
 #pragma unroll
             for (int q = 0; q < 7; ++q) slot[q * HP + hy * HX + hx] = m[q];
+            if (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) {
+                R* k0 = kz + (hy - 1) * kFX + (hx - 1);
+#pragma unroll
+                for (int p = 0; p < kQ; ++p) k0[p * KP] = d[p];
+#pragma unroll
+                for (int q = 0; q < 3 * kM; ++q) k0[(kQ + q) * KP] = gg[q];
+            }
         }
     };
 
@@ -615,12 +625,16 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
         const R* sm = ring + (size_t)(((z - 1) % kFRing + kFRing) % kFRing) * 7 * HP;
         const R* s0 = ring + (size_t)((z % kFRing)) * 7 * HP;
         const R* sp = ring + (size_t)(((z + 1) % kFRing)) * 7 * HP;
-#pragma unroll 1
-        for (int ly = warp; ly < th; ly += kFThreads / 32) {
-            if (lane >= tw) continue;
+        // phase B: one tile node per thread (warp = row, lane = column)
+        if (warp < th && lane < tw) {
+            const int ly = warp;
             const int x = x0 + lane, y = y0 + ly;
             R d[kQ], gg[3 * kM];
-            pull_node3<P>(src, g, x, y, z, d, gg);
+            const R* k0 = kept + (size_t)(z & 1) * kP * KP + ly * kFX + lane;
+#pragma unroll
+            for (int p = 0; p < kQ; ++p) d[p] = k0[p * KP];
+#pragma unroll
+            for (int q = 0; q < 3 * kM; ++q) gg[q] = k0[(kQ + q) * KP];
             const int c0 = (ly + 1) * HX + lane + 1;
             closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) {
                 const int o = q * HP;
@@ -637,6 +651,7 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
 #pragma unroll
             for (int q = 0; q < 3 * kM; ++q) dst[(kQ + q) * g.ps + node] = Fmt3<P>::enc(gg[q], kQ + q);
         }
+        __syncthreads();
     }
 }
 
@@ -812,12 +827,12 @@ cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
 // The fused form: tiles x segments work units, one CTA each.  The segment
 // count makes the units fill whole waves of the resident CTAs where it can
 // (each segment also pulls two planes of fields before its first plane).
-template <int P, int MODE, int TY>
+template <int P, int MODE>
 cudaError_t launch_fused3(const void* src, void* dst, const Geom3& g,
                           const Coll3<typename Fmt3<P>::R>& c, int resident, cudaStream_t st) {
     using S = typename Fmt3<P>::S;
     using R = typename Fmt3<P>::R;
-    const int tiles_x = (g.nx + kFX - 1) / kFX, tiles_y = (g.ny + TY - 1) / TY;
+    const int tiles_x = (g.nx + kFX - 1) / kFX, tiles_y = (g.ny + kFTY - 1) / kFTY;
     const long long tiles = (long long)tiles_x * tiles_y;
     int best_seg = 1;
     double best = -1.0;
@@ -837,23 +852,22 @@ cudaError_t launch_fused3(const void* src, void* dst, const Geom3& g,
     }
     const long long units = tiles * ((g.nz + best_seg - 1) / best_seg);
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)fused3_smem_floats<TY>() * sizeof(R);
-    fused3_kernel<P, MODE, TY><<<(unsigned)units, kFThreads, smem, st>>>(
-        (const S*)src, (S*)dst, g, tiles_x, tiles_y, best_seg, c);
+    const size_t smem = (size_t)fused3_smem_floats() * sizeof(R);
+    fused3_kernel<P, MODE><<<(unsigned)units, kFThreads, smem, st>>>((const S*)src, (S*)dst, g, tiles_x,
+                                                                       tiles_y, best_seg, c);
     return cudaGetLastError();
 }
 
-// Opt the fused kernel of one precision and closure in to its shared
-// memory; per_sm: its resident CTAs per SM.
+// Opt the fused kernel of one precision and closure in to its shared memory
+// (FP32 63 KB, FP64 126 KB); per_sm: its resident CTAs per SM.
 template <int P, int MODE>
 cudaError_t prepare_fused3_mode(int& per_sm) {
     using R = typename Fmt3<P>::R;
-    const size_t smem = (size_t)fused3_smem_floats<kFTY>() * sizeof(R);
-    cudaError_t e = cudaFuncSetAttribute(fused3_kernel<P, MODE, kFTY>,
+    const size_t smem = (size_t)fused3_smem_floats() * sizeof(R);
+    cudaError_t e = cudaFuncSetAttribute(fused3_kernel<P, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused3_kernel<P, MODE, kFTY>,
-                                                          kFThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused3_kernel<P, MODE>, kFThreads, smem);
     return e;
 }
 
@@ -865,8 +879,8 @@ cudaError_t prepare_fused3(int les, int& per_sm) {
 template <int P>
 cudaError_t launch_fused3_p(int les, const void* src, void* dst, const Geom3& g,
                             const Coll3<typename Fmt3<P>::R>& c, int resident, cudaStream_t st) {
-    return les == 2 ? launch_fused3<P, K3_FILTER, kFTY>(src, dst, g, c, resident, st)
-                    : launch_fused3<P, K3_CARATI, kFTY>(src, dst, g, c, resident, st);
+    return les == 2 ? launch_fused3<P, K3_FILTER>(src, dst, g, c, resident, st)
+                    : launch_fused3<P, K3_CARATI>(src, dst, g, c, resident, st);
 }
 
 }  // namespace d3

@@ -130,7 +130,7 @@ def test_launch_shapes_give_identical_bits(L, les):
 @pytest.mark.parametrize("shape", [(33, 17, 5), (70, 9, 3), (5, 3, 1), (1, 1, 1), (2, 2, 2),
                                    (40, 40, 40)])
 def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
-    """Ragged tiles (x not a multiple of 32, y not of 8), planes fewer than
+    """Ragged tiles (x not a multiple of 32, y not of 4), planes fewer than
     the ring, one-node and size-2 axes, and a lattice of many segments: the
     fused kernel's bits are the two-pass kernel's."""
     nx, ny, nz = shape
@@ -208,5 +208,5 @@ def test_refused_configurations(L):
         L.lbmhd3_set_launch(h, 0, 8)  # the fused kernel is for les 2, 3
     L.lbmhd3_destroy(h)
     h = L.lbmhd3_create(6, 4, 4, L.lbmhd_params_default(precision="fp32", les=2))
-    assert L.lbmhd3_get_launch(h) == (0, 8)  # FP32 closures default to the fused kernel
+    assert L.lbmhd3_get_launch(h) == (0, 4)  # FP32 closures default to the fused kernel
     L.lbmhd3_destroy(h)
