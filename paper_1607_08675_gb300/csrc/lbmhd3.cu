@@ -26,9 +26,12 @@
 // +z, -z), node (x, y, z) at (z ny + y) nx + x, plane stride padded to 64
 // elements.  f_i with i = 9 kz + 3 ky + kx, c = (v[kx], v[ky], v[kz]),
 // v = {0, 1, -1}.  Arithmetic in deviations d = f - w (g itself).
+#include <cuda_fp16.h>
+
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 
 #include "lbmhd_device.cuh"
 #include "lbmhd_internal.h"
@@ -64,18 +67,45 @@ __host__ __device__ constexpr R plane_rest3(int p) {
     return p < kQ ? wq<R>(p) : R(0);
 }
 
+// Storage formats: S stored, R arithmetic.  dec / enc convert a stored
+// value of plane p to and from its deviation d = f - w_p (g itself); sc is
+// the FP16 storage scale's inverse (dec) or the scale (enc), unused by the
+// other formats.  to_f / from_f convert to and from the population value f
+// in FP64 (initialisation and read-back).
 template <int P> struct Fmt3;
 template <> struct Fmt3<P_FP64> {
     using S = double;
     using R = double;
-    static __device__ __forceinline__ R dec(S v, int p) { return v - plane_rest3<R>(p); }
-    static __device__ __forceinline__ S enc(R d, int p) { return d + plane_rest3<R>(p); }
+    static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest3<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest3<R>(p); }
+    static __device__ __forceinline__ double to_f(S v, int, double) { return v; }
+    static __device__ __forceinline__ S from_f(double f, int, double) { return f; }
 };
 template <> struct Fmt3<P_FP32> {
     using S = float;
     using R = float;
-    static __device__ __forceinline__ R dec(S v, int p) { return v - plane_rest3<R>(p); }
-    static __device__ __forceinline__ S enc(R d, int p) { return d + plane_rest3<R>(p); }
+    static __device__ __forceinline__ R dec(S v, int p, float) { return v - plane_rest3<R>(p); }
+    static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest3<R>(p); }
+    static __device__ __forceinline__ double to_f(S v, int, double) { return (double)v; }
+    static __device__ __forceinline__ S from_f(double f, int, double) { return (float)f; }
+};
+// binary16 deviations times the storage scale (f - w_p, g itself), FP32
+// arithmetic
+template <> struct Fmt3<P_FP16_DEV> {
+    using S = unsigned short;
+    using R = float;
+    static __device__ __forceinline__ R dec(S v, int, float inv_s) {
+        return __half2float(__ushort_as_half(v)) * inv_s;
+    }
+    static __device__ __forceinline__ S enc(R d, int, float s) {
+        return __half_as_ushort(__float2half_rn(d * s));
+    }
+    static __device__ __forceinline__ double to_f(S v, int p, double inv_s) {
+        return (double)__half2float(__ushort_as_half(v)) * inv_s + plane_rest3<double>(p);
+    }
+    static __device__ __forceinline__ S from_f(double f, int p, double s) {
+        return __half_as_ushort(__float2half_rn((float)((f - plane_rest3<double>(p)) * s)));
+    }
 };
 
 template <class R>
@@ -83,6 +113,7 @@ struct Coll3 {
     R tn, te, tn2, te2, k18, k36;
     R d12;  // Delta^2 / 12 (les = 2)
     R cd2;  // C_S Delta^2 (les = 3)
+    float s16, i16;  // FP16 storage scale and its inverse
     int les;
 };
 
@@ -430,6 +461,85 @@ __device__ __forceinline__ void closure_collide3(R (&d)[kQ], R (&gg)[3 * kM], co
 // Pull + collide + store of V nodes.  MODE K3_FILTER / K3_CARATI read the
 // seven field planes mom (plane stride g.ps) at the six neighbours of each
 // node.  t >= total: a padding thread (valid addresses, no store).
+// FP16 storage, two nodes per thread: every plane is one 32-bit word per
+// thread (node x0 in the low half, x0 + 1 in the high half), the x-shifted
+// planes a funnel of half-words with the neighbouring lane's word
+// (byte_perm).  The word holds the two nodes' inputs and, once a node is
+// collided, its output in the same half, so the 45 planes take 45
+// registers instead of 90.
+template <int MODE>
+__device__ __forceinline__ void step3_body_h(const unsigned short* __restrict__ src,
+                                             unsigned short* __restrict__ dst, const Geom3 g,
+                                             unsigned t, unsigned total, const Coll3<float>& c,
+                                             const float* __restrict__ mom) {
+    const int lane = threadIdx.x & 31;
+    const bool live = t < total;
+    const unsigned tc = live ? t : total - 1;
+    const unsigned nxv = (unsigned)(g.nx / 2);
+    const unsigned row = tc / nxv;  // y + ny z
+    const int x0 = (int)(tc - row * nxv) * 2;
+    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    const bool has_left = lane > 0 && x0 > 0;
+    const bool has_right = lane < 31 && x0 + 2 < g.nx;
+    const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;
+    const int xr = x0 + 2 == g.nx ? 0 : x0 + 2;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    unsigned w[kP];
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+        const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
+        const int ry = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const int rz = cz == 0 ? z : (cz > 0 ? zm : zp);
+        const unsigned short* base = src + p * g.ps + ((long long)rz * g.ny + ry) * g.nx;
+        const unsigned own = *reinterpret_cast<const unsigned*>(base + x0);
+        if (cx == 0) {
+            w[p] = own;
+        } else if (cx > 0) {  // nodes x0 - 1, x0
+            unsigned prev = __shfl_up_sync(0xffffffffu, own, 1);
+            if (!has_left) prev = (unsigned)base[xl] << 16;
+            w[p] = __byte_perm(prev, own, 0x5432);
+        } else {  // nodes x0 + 1, x0 + 2
+            unsigned next = __shfl_down_sync(0xffffffffu, own, 1);
+            if (!has_right) next = (unsigned)base[xr];
+            w[p] = __byte_perm(own, next, 0x5432);
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+        const int sh = 16 * k;
+        float d[kQ], gg[3 * kM];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i)
+            d[i] = Fmt3<P_FP16_DEV>::dec((unsigned short)(w[i] >> sh), i, c.i16);
+#pragma unroll
+        for (int q = 0; q < 3 * kM; ++q)
+            gg[q] = Fmt3<P_FP16_DEV>::dec((unsigned short)(w[kQ + q] >> sh), kQ + q, c.i16);
+        if constexpr (MODE == K3_LOCAL) {
+            collide3<float>(d, gg, c);
+        } else {
+            const int x = x0 + k;
+            const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+            const long long rowo = ((long long)z * g.ny + y) * g.nx;
+            const long long nb[6] = {rowo + xp, rowo + xm, ((long long)z * g.ny + yp) * g.nx + x,
+                                     ((long long)z * g.ny + ym) * g.nx + x,
+                                     ((long long)zp * g.ny + y) * g.nx + x,
+                                     ((long long)zm * g.ny + y) * g.nx + x};
+            closure_collide3<float, MODE>(d, gg, c, [&](int q, int n) { return __ldg(mom + q * g.ps + nb[n]); });
+        }
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            const unsigned e = Fmt3<P_FP16_DEV>::enc(p < kQ ? d[p] : gg[p - kQ], p, c.s16);
+            w[p] = (w[p] & ~(0xffffu << sh)) | (e << sh);
+        }
+    }
+    if (live) {
+        const long long node = ((long long)z * g.ny + y) * g.nx + x0;
+#pragma unroll
+        for (int p = 0; p < kP; ++p) *reinterpret_cast<unsigned*>(dst + p * g.ps + node) = w[p];
+    }
+}
+
 template <int P, int V, int MODE>
 __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict__ src,
                                            typename Fmt3<P>::S* __restrict__ dst, const Geom3 g,
@@ -438,6 +548,10 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
                                            const typename Fmt3<P>::R* __restrict__ mom) {
     using S = typename Fmt3<P>::S;
     using R = typename Fmt3<P>::R;
+    if constexpr (P == P_FP16_DEV && V == 2) {
+        step3_body_h<MODE>(src, dst, g, t, total, c, mom);
+        return;
+    }
     const bool live = t < total;
     const unsigned tc = live ? t : total - 1;
     int x0, y, z;
@@ -447,9 +561,9 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
     for (int k = 0; k < V; ++k) {
         R d[kQ], gg[3 * kM];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i);
+        for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i, c.i16);
 #pragma unroll
-        for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q);
+        for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q, c.i16);
         if constexpr (MODE == K3_LOCAL) {
             collide3<R>(d, gg, c);
         } else {
@@ -465,9 +579,9 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
             closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) { return __ldg(mom + q * g.ps + nb[n]); });
         }
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) raw[i][k] = Fmt3<P>::enc(d[i], i);
+        for (int i = 0; i < kQ; ++i) raw[i][k] = Fmt3<P>::enc(d[i], i, c.s16);
 #pragma unroll
-        for (int q = 0; q < 3 * kM; ++q) raw[kQ + q][k] = Fmt3<P>::enc(gg[q], kQ + q);
+        for (int q = 0; q < 3 * kM; ++q) raw[kQ + q][k] = Fmt3<P>::enc(gg[q], kQ + q, c.s16);
     }
     if (live) {
         const long long node = ((long long)z * g.ny + y) * g.nx + x0;
@@ -486,7 +600,7 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
 template <int P, int V>
 __global__ void __launch_bounds__(256) mom3_kernel(const typename Fmt3<P>::S* __restrict__ src,
                                                    typename Fmt3<P>::R* __restrict__ mom, Geom3 g,
-                                                   unsigned total, unsigned total_pad) {
+                                                   unsigned total, unsigned total_pad, float i16) {
     using S = typename Fmt3<P>::S;
     using R = typename Fmt3<P>::R;
     const unsigned stride = gridDim.x * blockDim.x;
@@ -500,9 +614,9 @@ __global__ void __launch_bounds__(256) mom3_kernel(const typename Fmt3<P>::S* __
         for (int k = 0; k < V; ++k) {
             R d[kQ], gg[3 * kM], mk[7];
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i);
+            for (int i = 0; i < kQ; ++i) d[i] = Fmt3<P>::dec(raw[i][k], i, i16);
 #pragma unroll
-            for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q);
+            for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q][k], kQ + q, i16);
             fields3<R>(d, gg, mk);
 #pragma unroll
             for (int q = 0; q < 7; ++q) m[q][k] = mk[q];
@@ -556,7 +670,7 @@ __device__ __forceinline__ int wrap3i(int a, int n) { return a < 0 ? a + n : (a 
 template <int P>
 __device__ __forceinline__ void pull_node3(const typename Fmt3<P>::S* __restrict__ src, const Geom3& g,
                                            int x, int y, int z, typename Fmt3<P>::R (&d)[kQ],
-                                           typename Fmt3<P>::R (&gg)[3 * kM]) {
+                                           typename Fmt3<P>::R (&gg)[3 * kM], float i16) {
     const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
@@ -569,9 +683,9 @@ __device__ __forceinline__ void pull_node3(const typename Fmt3<P>::S* __restrict
         const unsigned off = ((unsigned)rz * (unsigned)g.ny + (unsigned)ry) * (unsigned)g.nx + (unsigned)rx;
         const auto v = __ldg(src + p * g.ps + off);
         if (p < kQ)
-            d[p] = Fmt3<P>::dec(v, p);
+            d[p] = Fmt3<P>::dec(v, p, i16);
         else
-            gg[p - kQ] = Fmt3<P>::dec(v, p);
+            gg[p - kQ] = Fmt3<P>::dec(v, p, i16);
     }
 }
 
@@ -603,7 +717,7 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
             const int hy = i / hw, hx = i - hy * hw;
             const int x = wrap3i(x0 - 1 + hx, g.nx), y = wrap3i(y0 - 1 + hy, g.ny);
             R d[kQ], gg[3 * kM], m[7];
-            pull_node3<P>(src, g, x, y, zw, d, gg);
+            pull_node3<P>(src, g, x, y, zw, d, gg, c.i16);
             fields3<R>(d, gg, m);
 #pragma unroll
             for (int q = 0; q < 7; ++q) slot[q * HP + hy * HX + hx] = m[q];
@@ -647,9 +761,9 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
             });
             const unsigned node = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) dst[i * g.ps + node] = Fmt3<P>::enc(d[i], i);
+            for (int i = 0; i < kQ; ++i) dst[i * g.ps + node] = Fmt3<P>::enc(d[i], i, c.s16);
 #pragma unroll
-            for (int q = 0; q < 3 * kM; ++q) dst[(kQ + q) * g.ps + node] = Fmt3<P>::enc(gg[q], kQ + q);
+            for (int q = 0; q < 3 * kM; ++q) dst[(kQ + q) * g.ps + node] = Fmt3<P>::enc(gg[q], kQ + q, c.s16);
         }
         __syncthreads();
     }
@@ -666,10 +780,21 @@ __global__ void __launch_bounds__(256) step3_kernel(const typename Fmt3<P>::S* _
         step3_body<P, V, MODE>(src, dst, g, t, total, c, mom);
 }
 
+// The FP16 two-node step without a closure, held to 128 registers (16 warps
+// per SM instead of 12; 8 bytes of spill).
+__global__ void __launch_bounds__(256, 2) step3h_kernel(const unsigned short* __restrict__ src,
+                                                        unsigned short* __restrict__ dst, Geom3 g,
+                                                        unsigned total, unsigned total_pad,
+                                                        Coll3<float> c) {
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride)
+        step3_body_h<K3_LOCAL>(src, dst, g, t, total, c, nullptr);
+}
+
 // Equilibrium initialisation from seven FP64 device fields.
 template <int P>
 __global__ void init3_kernel(const double* __restrict__ f7, long long n,
-                             typename Fmt3<P>::S* __restrict__ st, long long ps) {
+                             typename Fmt3<P>::S* __restrict__ st, long long ps, double s16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double rho = f7[i], u[3] = {f7[n + i], f7[2 * n + i], f7[3 * n + i]},
@@ -684,7 +809,7 @@ __global__ void init3_kernel(const double* __restrict__ f7, long long n,
             const double w = wq<double>(p);
             const double f = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) +
                              4.5 * w * (0.5 * bb * (cx * cx + cy * cy + cz * cz) - cb * cb - bb / 6.0);
-            st[p * ps + i] = (typename Fmt3<P>::S)f;
+            st[p * ps + i] = Fmt3<P>::from_f(f, p, s16);
         }
 #pragma unroll
         for (int q = 0; q < kM; ++q) {
@@ -692,8 +817,8 @@ __global__ void init3_kernel(const double* __restrict__ f7, long long n,
             const double sg = q % 2 ? -1.0 : 1.0;
 #pragma unroll
             for (int b = 0; b < 3; ++b)
-                st[(kQ + 3 * q + b) * ps + i] = (typename Fmt3<P>::S)(
-                    (B[b] + 3.0 * sg * (u[a] * B[b] - B[a] * u[b])) / 6.0);
+                st[(kQ + 3 * q + b) * ps + i] = Fmt3<P>::from_f(
+                    (B[b] + 3.0 * sg * (u[a] * B[b] - B[a] * u[b])) / 6.0, kQ + 3 * q + b, s16);
         }
     }
 }
@@ -701,13 +826,13 @@ __global__ void init3_kernel(const double* __restrict__ f7, long long n,
 // rho, u (3), B (3) of the stored state into seven FP64 fields.
 template <int P>
 __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps,
-                                long long n, double* __restrict__ m7) {
+                                long long n, double* __restrict__ m7, double i16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int p = 0; p < kQ; ++p) {
-            const double f = (double)st[p * ps + i];
+            const double f = Fmt3<P>::to_f(st[p * ps + i], p, i16);
             rho += f;
             j[0] += pcx(p) * f;
             j[1] += pcy(p) * f;
@@ -716,7 +841,7 @@ __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long
 #pragma unroll
         for (int q = 0; q < kM; ++q)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) B[b] += (double)st[(kQ + 3 * q + b) * ps + i];
+            for (int b = 0; b < 3; ++b) B[b] += Fmt3<P>::to_f(st[(kQ + 3 * q + b) * ps + i], kQ + 3 * q + b, i16);
         m7[i] = rho;
         for (int a = 0; a < 3; ++a) {
             m7[(1 + a) * n + i] = j[a] / rho;
@@ -728,11 +853,11 @@ __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long
 // The stored state decoded to 45 FP64 planes of n.
 template <int P>
 __global__ void get3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps, long long n,
-                            double* __restrict__ out) {
+                            double* __restrict__ out, double i16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
 #pragma unroll
-        for (int p = 0; p < kP; ++p) out[p * n + i] = (double)st[p * ps + i];
+        for (int p = 0; p < kP; ++p) out[p * n + i] = Fmt3<P>::to_f(st[p * ps + i], p, i16);
 }
 
 // Diagnostics from the moment fields: per block, FP64 sums in a fixed order
@@ -808,7 +933,7 @@ cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
     const unsigned total_pad = (total + 31u) / 32u * 32u;
     const unsigned blocks = (total_pad + block - 1) / block;
     if (les == 2 || les == 3) {
-        mom3_kernel<P, V><<<blocks, block, 0, st>>>((const S*)src, (R*)mom, g, total, total_pad);
+        mom3_kernel<P, V><<<blocks, block, 0, st>>>((const S*)src, (R*)mom, g, total, total_pad, c.i16);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (les == 2)
@@ -819,8 +944,11 @@ cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
                                                                    total_pad, c, (const R*)mom);
         return cudaGetLastError();
     }
-    step3_kernel<P, V, K3_LOCAL><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
-                                                           total_pad, c, nullptr);
+    if constexpr (P == P_FP16_DEV && V == 2)
+        step3h_kernel<<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total, total_pad, c);
+    else
+        step3_kernel<P, V, K3_LOCAL><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
+                                                               total_pad, c, nullptr);
     return cudaGetLastError();
 }
 
@@ -933,6 +1061,15 @@ int check3(lbmhd3_t* h) {
     return LBMHD_OK;
 }
 
+// Calls f(std::integral_constant<int, P>{}) for the handle's storage format.
+template <class F>
+cudaError_t by_prec3(int prec, F f) {
+    if (prec == LBMHD_FP64) return f(std::integral_constant<int, P_FP64>{});
+    if (prec == LBMHD_FP32) return f(std::integral_constant<int, P_FP32>{});
+    if (prec == LBMHD_FP16_DEV) return f(std::integral_constant<int, P_FP16_DEV>{});
+    return cudaErrorInvalidValue;
+}
+
 template <class R>
 Coll3<R> coll3(const lbmhd_params& p) {
     Coll3<R> c;
@@ -945,6 +1082,8 @@ Coll3<R> coll3(const lbmhd_params& p) {
     c.k36 = (R)(36.0 * cd2);
     c.d12 = (R)(p.delta * p.delta / 12.0);
     c.cd2 = (R)cd2;
+    c.s16 = (float)p.fp16_scale;
+    c.i16 = (float)(1.0 / p.fp16_scale);
     c.les = p.les == 1 ? 1 : 0;
     return c;
 }
@@ -954,32 +1093,37 @@ long long nodes3(const lbmhd3_t* h) { return (long long)h->geom.nx * h->geom.ny 
 cudaError_t one_step3(lbmhd3_t* h) {
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
-    cudaError_t e = cudaErrorInvalidValue;
     const int les = h->p.les;
-    if (h->vec == 0) {
-        e = h->p.precision == LBMHD_FP64
-                ? launch_fused3_p<P_FP64>(les, src, dst, h->geom, coll3<double>(h->p), h->fused_resident, h->stream)
-                : launch_fused3_p<P_FP32>(les, src, dst, h->geom, coll3<float>(h->p), h->fused_resident, h->stream);
-        if (e == cudaSuccess) {
-            h->cur = 1 - h->cur;
-            ++h->launches;
-        }
-        return e;
-    }
-    if (h->p.precision == LBMHD_FP64)
-        e = h->vec == 2 ? launch3_pv<P_FP64, 2>(h->block, src, dst, h->geom, coll3<double>(h->p), les, h->mom, h->stream)
-                        : launch3_pv<P_FP64, 1>(h->block, src, dst, h->geom, coll3<double>(h->p), les, h->mom, h->stream);
-    else
-        e = h->vec == 2 ? launch3_pv<P_FP32, 2>(h->block, src, dst, h->geom, coll3<float>(h->p), les, h->mom, h->stream)
-                        : launch3_pv<P_FP32, 1>(h->block, src, dst, h->geom, coll3<float>(h->p), les, h->mom, h->stream);
+    const cudaError_t e = by_prec3(h->p.precision, [&](auto tag) {
+        constexpr int P = decltype(tag)::value;
+        using R = typename Fmt3<P>::R;
+        const Coll3<R> c = coll3<R>(h->p);
+        if (h->vec == 0) return launch_fused3_p<P>(les, src, dst, h->geom, c, h->fused_resident, h->stream);
+        return h->vec == 2 ? launch3_pv<P, 2>(h->block, src, dst, h->geom, c, les, h->mom, h->stream)
+                           : launch3_pv<P, 1>(h->block, src, dst, h->geom, c, les, h->mom, h->stream);
+    });
     if (e == cudaSuccess) {
         h->cur = 1 - h->cur;
-        h->launches += les >= 2 ? 2 : 1;
+        h->launches += les >= 2 && h->vec != 0 ? 2 : 1;
     }
     return e;
 }
 
-size_t value3_bytes(int prec) { return prec == LBMHD_FP64 ? 8 : (prec == LBMHD_FP32 ? 4 : 0); }
+// rho, u, B of the current state into seven FP64 device fields.
+cudaError_t moments3_into(lbmhd3_t* h, double* m7) {
+    const long long n = (long long)h->geom.nx * h->geom.ny * h->geom.nz;
+    return by_prec3(h->p.precision, [&](auto tag) {
+        constexpr int P = decltype(tag)::value;
+        using S = typename Fmt3<P>::S;
+        moments3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>((const S*)h->buf[h->cur], h->geom.ps, n,
+                                                                  m7, 1.0 / h->p.fp16_scale);
+        return cudaGetLastError();
+    });
+}
+
+size_t value3_bytes(int prec) {
+    return prec == LBMHD_FP64 ? 8 : (prec == LBMHD_FP32 ? 4 : (prec == LBMHD_FP16_DEV ? 2 : 0));
+}
 
 }  // namespace
 
@@ -994,7 +1138,9 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 30))
         return fail3(LBMHD_EINVAL, "nx, ny, nz must be >= 1 with nx*ny*nz <= 2^30 nodes");
     if (value3_bytes(p->precision) == 0)
-        return fail3(LBMHD_EINVAL, "3D lattices: FP64 or FP32 storage");
+        return fail3(LBMHD_EINVAL, "3D lattices: FP64, FP32 or FP16 deviation storage");
+    if (p->precision == LBMHD_FP16_DEV && !(p->fp16_scale > 0.0 && p->fp16_scale < 1e30))
+        return fail3(LBMHD_EINVAL, "fp16_scale must be positive and finite");
     if (p->les < 0 || p->les > 3)
         return fail3(LBMHD_EINVAL,
                      "les must be 0 (off), 1 (local rates), 2 (filtered equilibria) or 3 "
@@ -1028,7 +1174,8 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
         h->own_stream = true;
     }
     const size_t bytes = (size_t)kP * h->geom.ps * value3_bytes(p->precision);
-    const size_t mbytes = p->les >= 2 ? (size_t)7 * h->geom.ps * value3_bytes(p->precision) : 0;
+    // field planes in the arithmetic type: FP64, or FP32 for the FP32 and FP16 formats
+    const size_t mbytes = p->les >= 2 ? (size_t)7 * h->geom.ps * (p->precision == LBMHD_FP64 ? 8 : 4) : 0;
     void** bufs[3] = {&h->buf[0], &h->buf[1], &h->mom};
     const size_t sizes[3] = {bytes, bytes, mbytes};
     for (int b = 0; b < 3; ++b) {
@@ -1050,14 +1197,15 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     // registers in FP64).
     h->vec = nx % 2 == 0 && p->les < 2 ? 2 : 1;
     h->block = 128;
-    if (p->les >= 2 && p->precision == LBMHD_FP32) {  // the fused one-pass kernel
+    if (p->les >= 2 && p->precision != LBMHD_FP64) {  // the fused one-pass kernel
         h->vec = 0;
         h->block = kFTY;
     }
     if (p->les >= 2) {
         int per_sm = 0, nsm = 0;
-        e = p->precision == LBMHD_FP64 ? prepare_fused3<P_FP64>(p->les, per_sm)
-                                       : prepare_fused3<P_FP32>(p->les, per_sm);
+        e = by_prec3(p->precision, [&](auto tag) {
+            return prepare_fused3<decltype(tag)::value>(p->les, per_sm);
+        });
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
         if (e != cudaSuccess) {
             lbmhd3_destroy(h);
@@ -1110,11 +1258,12 @@ int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* 
     for (int i = 0; i < 7; ++i)
         LBMHD3_CK(h, cudaMemcpyAsync(tmp + i * n, f[i], n * sizeof(double), cudaMemcpyHostToDevice,
                                      h->stream));
-    if (h->p.precision == LBMHD_FP64)
-        init3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>(tmp, n, (double*)h->buf[h->cur], h->geom.ps);
-    else
-        init3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>(tmp, n, (float*)h->buf[h->cur], h->geom.ps);
-    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, by_prec3(h->p.precision, [&](auto tag) {
+                  constexpr int P = decltype(tag)::value;
+                  init3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>(
+                      tmp, n, (typename Fmt3<P>::S*)h->buf[h->cur], h->geom.ps, h->p.fp16_scale);
+                  return cudaGetLastError();
+              }));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
@@ -1142,11 +1291,7 @@ int lbmhd3_moments(lbmhd3_t* h, double* out7) {
     const long long n = nodes3(h);
     double* tmp = nullptr;
     LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, 7 * n * sizeof(double), h->stream));
-    if (h->p.precision == LBMHD_FP64)
-        moments3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, tmp);
-    else
-        moments3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, tmp);
-    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, moments3_into(h, tmp));
     LBMHD3_CK(h, cudaMemcpyAsync(out7, tmp, 7 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
@@ -1161,11 +1306,12 @@ int lbmhd3_get_state(lbmhd3_t* h, double* out) {
     const long long n = nodes3(h);
     double* tmp = nullptr;
     LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, (size_t)kP * n * sizeof(double), h->stream));
-    if (h->p.precision == LBMHD_FP64)
-        get3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, tmp);
-    else
-        get3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, tmp);
-    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, by_prec3(h->p.precision, [&](auto tag) {
+                  constexpr int P = decltype(tag)::value;
+                  get3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>(
+                      (const typename Fmt3<P>::S*)h->buf[h->cur], h->geom.ps, n, tmp, 1.0 / h->p.fp16_scale);
+                  return cudaGetLastError();
+              }));
     LBMHD3_CK(h, cudaMemcpyAsync(out, tmp, (size_t)kP * n * sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
@@ -1184,11 +1330,7 @@ int lbmhd3_diagnostics(lbmhd3_t* h, double* out12) {
         LBMHD3_CK(h, cudaMalloc((void**)&h->d_rows, kDiagRows3 * 12 * sizeof(double)));
         LBMHD3_CK(h, cudaMalloc((void**)&h->d_out, 12 * sizeof(double)));
     }
-    if (h->p.precision == LBMHD_FP64)
-        moments3_kernel<P_FP64><<<grid3(n, 256), 256, 0, h->stream>>>((const double*)h->buf[h->cur], h->geom.ps, n, h->d_m7);
-    else
-        moments3_kernel<P_FP32><<<grid3(n, 256), 256, 0, h->stream>>>((const float*)h->buf[h->cur], h->geom.ps, n, h->d_m7);
-    LBMHD3_CK(h, cudaGetLastError());
+    LBMHD3_CK(h, moments3_into(h, h->d_m7));
     long long nb = (n + kDiagBlock3 - 1) / kDiagBlock3;
     if (nb > kDiagRows3) nb = kDiagRows3;
     diag3_kernel<<<(unsigned)nb, kDiagBlock3, 0, h->stream>>>(h->d_m7, h->geom, h->d_rows);

@@ -1,6 +1,7 @@
 """The 3D step (D3Q27 + D3Q7) on the GPU against the 3D oracle, through the
 lbmhd3_* C ABI: every population plane and the moments after many steps on
-ragged lattices (FP64 to the 1e-12 bar, FP32 to its storage bar), with LES
+ragged lattices (FP64 to the 1e-12 bar, FP32 and FP16 deviation storage to
+their storage bars), with LES
 off, the local LES rates, the paper's filtered equilibria (kinetic LES) and
 the cross-helicity closure; identical bits across launch shapes; the
 diagnostics; one step at sampled nodes of a larger lattice in the default
@@ -114,13 +115,50 @@ def test_fp32_matches_oracle(L, o3, les):
     assert max(e.values()) < 2e-4, e
 
 
+@pytest.mark.parametrize("les", [0, 1, 2, 3])
+def test_fp16_deviations_match_oracle(L, o3, les):
+    """FP16 storage of the deviations f - w (g itself) times the storage
+    scale 1024, FP32 arithmetic: 100 steps within 2e-3 of the FP64 oracle
+    per field relative to its maximum (measured up to 7.8e-4: the binary16
+    rounding, 2^-11 relative, of every stored deviation each step)."""
+    fields = inputs.turbulence3d(16, 12, 10, kmin=1, kmax=3, rms=0.05, seed=9)
+    kw = dict(KW, les=les, precision="fp16_dev")
+    ref = o3.step(o3.init(*fields), o3.params(**okw(kw)), 100)
+    m, _, _ = gpu3(L, fields, 100, **kw)
+    e = rel_fields(m, o3.moments(ref))
+    assert max(e.values()) < 2e-3, e
+
+
+def test_fp16_one_step_is_the_rounded_oracle_step(L, o3):
+    """One step from a developed FP16 state: every population of every
+    node is the oracle's step of the same stored state (decoded exactly)
+    up to the binary16 rounding of its deviation (half an ulp, 2^-11
+    relative) and the FP32 arithmetic."""
+    nx, ny, nz = 24, 10, 8
+    fields = inputs.turbulence3d(nx, ny, nz, kmin=1, kmax=3, rms=0.05, seed=3)
+    c, w, _, _ = o3.lattice()
+    rest = np.concatenate([w, np.zeros(18)])[:, None, None, None]
+    for les in (1, 2, 3):
+        kw = dict(KW, les=les, precision="fp16_dev")
+        h = L.lbmhd3_create(nx, ny, nz, L.lbmhd_params_default(**kw))
+        L.lbmhd3_init(h, *fields)
+        L.lbmhd3_step(h, 10)
+        before = L.lbmhd3_get_state(h)
+        L.lbmhd3_step(h, 1)
+        after = L.lbmhd3_get_state(h)
+        L.lbmhd3_destroy(h)
+        ref = o3.step(before, o3.params(**okw(kw)), 1)
+        bound = 2.0 ** -11 * np.abs(ref - rest) + 2e-7
+        assert np.all(np.abs(after - ref) <= bound), (les, np.max(np.abs(after - ref) - bound))
+
+
 @pytest.mark.parametrize("les", [1, 2, 3])
 def test_launch_shapes_give_identical_bits(L, les):
     fields = inputs.turbulence3d(32, 8, 6, seed=2)
     shapes = ((1, 128), (2, 128), (1, 64), (2, 256))
     if les >= 2:  # and the fused one-pass kernel
         shapes += ((0, 8),)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp16_dev"):
         sts = [gpu3(L, fields, 30, vec, block, precision=prec, **dict(KW, les=les))[1]
                for vec, block in shapes]
         assert all(np.array_equal(sts[0], s) for s in sts[1:]), (prec, les)
@@ -137,7 +175,7 @@ def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
     rng = np.random.default_rng(nx + ny + nz)
     fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
         0.02 * rng.standard_normal((nz, ny, nx)) for _ in range(6))
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64", "fp16_dev"):
         kw = dict(KW, les=les, precision=prec)
         ref = gpu3(L, fields, 12, 1, 128, **kw)[1]
         got = gpu3(L, fields, 12, 0, 8, **kw)[1]
@@ -194,8 +232,8 @@ def test_sampled_step_of_a_larger_lattice(L, o3, les):
 
 
 def test_refused_configurations(L):
-    for bad in (dict(les=4), dict(les=-1), dict(precision="fp16_dev"), dict(precision="ff"),
-                dict(tau_nu=0.5)):
+    for bad in (dict(les=4), dict(les=-1), dict(precision="fp32_dev"), dict(precision="ff"),
+                dict(tau_nu=0.5), dict(precision="fp16_dev", fp16_scale=0.0)):
         with pytest.raises(L.LBMHDError) as e:
             L.lbmhd3_create(8, 8, 8, L.lbmhd_params_default(**dict(dict(precision="fp32"), **bad)))
         assert e.value.code == -1
