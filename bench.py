@@ -687,7 +687,8 @@ def run_ours(args):
     if not args.no_variants:
         from paper_1607_08675_gb300 import inputs
 
-        for vp, n3 in (("fp32", args.n3), ("fp16_dev", args.n3), ("fp64", max(16, args.n3 // 2))):
+        for vp, n3 in (("fp32", args.n3), ("fp16_dev", args.n3), ("fp64", max(16, args.n3 // 2)),
+                       ("ff", max(16, args.n3 // 2))):
             h3 = L.lbmhd3_create(n3, n3, n3, L.lbmhd_params_default(
                 precision=vp, tau_nu=0.51, tau_eta=0.51, C_S=0.1, les=1, stream=stream))
             L.lbmhd3_init(h3, *inputs.turbulence3d(n3, n3, n3, seed=1 + rank))

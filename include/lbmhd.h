@@ -371,8 +371,10 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * collision (the paper's MRT with all rates tied) and magnetic SRT, with the
  * local Smagorinsky rates (les 1) from the traceless non-equilibrium stress
  * and the axial vector of the magnetic non-equilibrium first moment.
- * Storage: FP64, FP32 or FP16 deviations (binary16 (f - w_i) times
- * fp16_scale, g times fp16_scale; FP32 arithmetic), 45 planes (27 f_i with i = 9 kz + 3 ky + kx,
+ * Storage: FP64, FP32, FP16 deviations (binary16 (f - w_i) times
+ * fp16_scale, g times fp16_scale; FP32 arithmetic) or double-word
+ * deviations (FF: (hi, lo) FP32 pairs, double-word arithmetic), 45 planes
+ * (27 f_i with i = 9 kz + 3 ky + kx,
  * c = (v[kx], v[ky], v[kz]), v = {0, 1, -1}; then g_q (x, y, z) for
  * q = +x, -x, +y, -y, +z, -z), node (x, y, z) at (z ny + y) nx + x.  Host
  * fields: FP64 arrays of nx*ny*nz, x fastest, caller-owned.  Periodic in
@@ -385,7 +387,7 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * closure's relaxation times (Eqs. CHClosureV/B with 3D strain and curl). */
 typedef struct lbmhd3_t lbmhd3_t;
 
-/* Uses precision (FP64, FP32 or FP16_DEV with fp16_scale), tau_nu, tau_eta, C_S, delta, les (0 off,
+/* Uses precision (FP64, FP32, FP16_DEV with fp16_scale, or FF), tau_nu, tau_eta, C_S, delta, les (0 off,
  * 1 local rates, 2 filtered equilibria, 3 cross-helicity closure) and stream
  * of p.  Allocates two state buffers, and for les 2, 3 seven field planes.
  * EINVAL for other precisions or closures, tau <= 1/2, more than 2^30

@@ -66,6 +66,28 @@ template <class R>
 __host__ __device__ constexpr R plane_rest3(int p) {
     return p < kQ ? wq<R>(p) : R(0);
 }
+// The weight in the arithmetic type: FP32 and FP64 form the product in
+// their own arithmetic, double-word takes the nearest double-word to the
+// FP64 product (exact to 2^-48).
+template <class R>
+__device__ __forceinline__ R wqr(int i) {
+    if constexpr (std::is_same<R, ff>::value)
+        return ff(wq<double>(i));
+    else
+        return wq<R>(i);
+}
+__device__ __forceinline__ ff fmax(ff a, ff b) { return a > b ? a : b; }
+using ::fmax;
+// A read-only load of a value of the arithmetic type.
+template <class R>
+__device__ __forceinline__ R ldg_r(const R* p) {
+    if constexpr (std::is_same<R, ff>::value) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return ff(v.x, v.y);
+    } else {
+        return __ldg(p);
+    }
+}
 
 // Storage formats: S stored, R arithmetic.  dec / enc convert a stored
 // value of plane p to and from its deviation d = f - w_p (g itself); sc is
@@ -88,6 +110,21 @@ template <> struct Fmt3<P_FP32> {
     static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest3<R>(p); }
     static __device__ __forceinline__ double to_f(S v, int, double) { return (double)v; }
     static __device__ __forceinline__ S from_f(double f, int, double) { return (float)f; }
+};
+// double-word deviations (hi, lo) of f - w_p (g itself), double-word
+// arithmetic (the FP32 pipes)
+template <> struct Fmt3<P_FF> {
+    using S = float2;
+    using R = ff;
+    static __device__ __forceinline__ R dec(S v, int, float) { return ff(v.x, v.y); }
+    static __device__ __forceinline__ S enc(R d, int, float) { return make_float2(d.hi, d.lo); }
+    static __device__ __forceinline__ double to_f(S v, int p, double) {
+        return ((double)v.x + (double)v.y) + plane_rest3<double>(p);
+    }
+    static __device__ __forceinline__ S from_f(double f, int p, double) {
+        const ff d(f - plane_rest3<double>(p));
+        return make_float2(d.hi, d.lo);
+    }
 };
 // binary16 deviations times the storage scale (f - w_p, g itself), FP32
 // arithmetic
@@ -266,7 +303,7 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
             if (cy && cz) qf += cy * cz > 0 ? q2[2] : -q2[2];
             R t = fmad(R(3), cj, cc ? fmad(hh, R(cc), base) : base);
             t = fmad(R(4.5), qf, t);
-            const R deq = wq<R>(i) * t;
+            const R deq = wqr<R>(i) * t;
             d[i] = fmad(-s, d[i] - deq, d[i]);
         }
 #pragma unroll
@@ -312,7 +349,7 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
         const int cc = cx * cx + cy * cy + cz * cz;
         R t = fmad(R(3), cj, cc ? fmad(half_bb, R(cc), base) : base);
         t = fmad(k45 * cj, cj, fmad(R(-4.5) * cb, cb, t));
-        const R deq = wq<R>(i) * t;
+        const R deq = wqr<R>(i) * t;
         d[i] = fmad(-s, d[i] - deq, d[i]);
     }
     // magnetic: g_q^eq = (1/6) [B + 3 ((C.u) B - (C.B) u)]
@@ -576,7 +613,7 @@ __device__ __forceinline__ void step3_body(const typename Fmt3<P>::S* __restrict
                                      ((long long)z * g.ny + ym) * g.nx + x,
                                      ((long long)zp * g.ny + y) * g.nx + x,
                                      ((long long)zm * g.ny + y) * g.nx + x};
-            closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) { return __ldg(mom + q * g.ps + nb[n]); });
+            closure_collide3<R, MODE>(d, gg, c, [&](int q, int n) { return ldg_r(mom + q * g.ps + nb[n]); });
         }
 #pragma unroll
         for (int i = 0; i < kQ; ++i) raw[i][k] = Fmt3<P>::enc(d[i], i, c.s16);
@@ -690,7 +727,7 @@ __device__ __forceinline__ void pull_node3(const typename Fmt3<P>::S* __restrict
 }
 
 template <int P, int MODE>
-__global__ void __launch_bounds__(kFThreads, P == P_FP64 ? 1 : 3)
+__global__ void __launch_bounds__(kFThreads, P == P_FP64 || P == P_FF ? 1 : 3)
     fused3_kernel(const typename Fmt3<P>::S* __restrict__ src, typename Fmt3<P>::S* __restrict__ dst,
                   Geom3 g, int tiles_x, int tiles_y, int seglen, Coll3<typename Fmt3<P>::R> c) {
     using R = typename Fmt3<P>::R;
@@ -1067,6 +1104,7 @@ cudaError_t by_prec3(int prec, F f) {
     if (prec == LBMHD_FP64) return f(std::integral_constant<int, P_FP64>{});
     if (prec == LBMHD_FP32) return f(std::integral_constant<int, P_FP32>{});
     if (prec == LBMHD_FP16_DEV) return f(std::integral_constant<int, P_FP16_DEV>{});
+    if (prec == LBMHD_FF) return f(std::integral_constant<int, P_FF>{});
     return cudaErrorInvalidValue;
 }
 
@@ -1122,7 +1160,8 @@ cudaError_t moments3_into(lbmhd3_t* h, double* m7) {
 }
 
 size_t value3_bytes(int prec) {
-    return prec == LBMHD_FP64 ? 8 : (prec == LBMHD_FP32 ? 4 : (prec == LBMHD_FP16_DEV ? 2 : 0));
+    return prec == LBMHD_FP64 || prec == LBMHD_FF ? 8
+                                                  : (prec == LBMHD_FP32 ? 4 : (prec == LBMHD_FP16_DEV ? 2 : 0));
 }
 
 }  // namespace
@@ -1138,7 +1177,7 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 30))
         return fail3(LBMHD_EINVAL, "nx, ny, nz must be >= 1 with nx*ny*nz <= 2^30 nodes");
     if (value3_bytes(p->precision) == 0)
-        return fail3(LBMHD_EINVAL, "3D lattices: FP64, FP32 or FP16 deviation storage");
+        return fail3(LBMHD_EINVAL, "3D lattices: FP64, FP32, FP16 deviation or double-word storage");
     if (p->precision == LBMHD_FP16_DEV && !(p->fp16_scale > 0.0 && p->fp16_scale < 1e30))
         return fail3(LBMHD_EINVAL, "fp16_scale must be positive and finite");
     if (p->les < 0 || p->les > 3)
@@ -1175,7 +1214,8 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     }
     const size_t bytes = (size_t)kP * h->geom.ps * value3_bytes(p->precision);
     // field planes in the arithmetic type: FP64, or FP32 for the FP32 and FP16 formats
-    const size_t mbytes = p->les >= 2 ? (size_t)7 * h->geom.ps * (p->precision == LBMHD_FP64 ? 8 : 4) : 0;
+    const size_t mbytes =
+        p->les >= 2 ? (size_t)7 * h->geom.ps * (p->precision == LBMHD_FP64 || p->precision == LBMHD_FF ? 8 : 4) : 0;
     void** bufs[3] = {&h->buf[0], &h->buf[1], &h->mom};
     const size_t sizes[3] = {bytes, bytes, mbytes};
     for (int b = 0; b < 3; ++b) {
@@ -1195,9 +1235,9 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     // by its FP64 arithmetic, where the fused kernel measured slower) the
     // two-pass kernels one node per thread (two nodes need more than 255
     // registers in FP64).
-    h->vec = nx % 2 == 0 && p->les < 2 ? 2 : 1;
+    h->vec = nx % 2 == 0 && p->les < 2 && p->precision != LBMHD_FF ? 2 : 1;
     h->block = 128;
-    if (p->les >= 2 && p->precision != LBMHD_FP64) {  // the fused one-pass kernel
+    if (p->les >= 2 && p->precision != LBMHD_FP64 && p->precision != LBMHD_FF) {  // the fused kernel
         h->vec = 0;
         h->block = kFTY;
     }

@@ -116,6 +116,23 @@ def test_fp32_matches_oracle(L, o3, les):
 
 
 @pytest.mark.parametrize("les", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(12, 10, 8), (16, 6, 9)])
+def test_double_word_matches_oracle(L, o3, les, shape):
+    """Double-word deviations (hi + lo of two FP32 numbers, unit roundoff
+    2^-48) on the FP32 pipes: the FP64 bars times 2^5, the ratio of the
+    unit roundoffs -- moments 3.2e-11 relative to their maxima after 100
+    steps, every population 3.2e-13."""
+    nx, ny, nz = shape
+    fields = inputs.turbulence3d(nx, ny, nz, kmin=1, kmax=2, rms=0.05, seed=nx)
+    kw = dict(KW, les=les, precision="ff")
+    ref = o3.step(o3.init(*fields), o3.params(**okw(kw)), 100)
+    m, st, _ = gpu3(L, fields, 100, **kw)
+    e = rel_fields(m, o3.moments(ref))
+    assert max(e.values()) < 3.2e-11, e
+    assert np.max(np.abs(st - ref)) < 3.2e-13, np.max(np.abs(st - ref))
+
+
+@pytest.mark.parametrize("les", [0, 1, 2, 3])
 def test_fp16_deviations_match_oracle(L, o3, les):
     """FP16 storage of the deviations f - w (g itself) times the storage
     scale 1024, FP32 arithmetic: 100 steps within 2e-3 of the FP64 oracle
@@ -158,7 +175,7 @@ def test_launch_shapes_give_identical_bits(L, les):
     shapes = ((1, 128), (2, 128), (1, 64), (2, 256))
     if les >= 2:  # and the fused one-pass kernel
         shapes += ((0, 8),)
-    for prec in ("fp64", "fp32", "fp16_dev"):
+    for prec in ("fp64", "fp32", "fp16_dev", "ff"):
         sts = [gpu3(L, fields, 30, vec, block, precision=prec, **dict(KW, les=les))[1]
                for vec, block in shapes]
         assert all(np.array_equal(sts[0], s) for s in sts[1:]), (prec, les)
@@ -175,7 +192,7 @@ def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
     rng = np.random.default_rng(nx + ny + nz)
     fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
         0.02 * rng.standard_normal((nz, ny, nx)) for _ in range(6))
-    for prec in ("fp32", "fp64", "fp16_dev"):
+    for prec in ("fp32", "fp64", "fp16_dev", "ff"):
         kw = dict(KW, les=les, precision=prec)
         ref = gpu3(L, fields, 12, 1, 128, **kw)[1]
         got = gpu3(L, fields, 12, 0, 8, **kw)[1]
@@ -232,8 +249,8 @@ def test_sampled_step_of_a_larger_lattice(L, o3, les):
 
 
 def test_refused_configurations(L):
-    for bad in (dict(les=4), dict(les=-1), dict(precision="fp32_dev"), dict(precision="ff"),
-                dict(tau_nu=0.5), dict(precision="fp16_dev", fp16_scale=0.0)):
+    for bad in (dict(les=4), dict(les=-1), dict(precision="fp32_dev"), dict(tau_nu=0.5),
+                dict(precision="fp16_dev", fp16_scale=0.0)):
         with pytest.raises(L.LBMHDError) as e:
             L.lbmhd3_create(8, 8, 8, L.lbmhd_params_default(**dict(dict(precision="fp32"), **bad)))
         assert e.value.code == -1
