@@ -917,6 +917,94 @@ def run_decomp(args):
         dist.destroy_process_group()
 
 
+def run_decomp3(args):
+    """One n3^3 lattice cut into z-slabs (decomp.SlabRunner3): slab s on
+    rank s * world // k, halos over NCCL between ranks, the planes that need
+    no ghost plane computed while the halo is in flight; value = lattice
+    node updates per second of the job (strong scaling)."""
+    import torch
+
+    from paper_1607_08675_gb300 import build, decomp, inputs, lbmhd as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    L.lib()
+    n, prec = args.n3, args.precision
+    les = args.les or 1
+    k = args.decomp_slabs or world
+    owner = [s * world // k for s in range(k)]
+    mine = [s for s in range(k) if owner[s] == rank]
+    kw = dict(tau_nu=0.51, tau_eta=0.51, C_S=0.1, precision=prec, les=les, delta=2.0)
+    runner = decomp.SlabRunner3(n, n, n, k, slabs=mine,
+                                comm=decomp.DistComm(owner) if world > 1 else None,
+                                overlap=not args.no_overlap, **kw)
+    runner.init(*inputs.turbulence3d(n, n, n, seed=1))
+    hbm, _ = peaks()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    runner.step(args.warmup)
+    barrier()
+    launches0 = sum(L.lbmhd3_launch_count(h) for h in runner.h.values())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_id_for_smi()) as clk:
+        barrier()
+        e0.record(runner.main)
+        runner.step(args.steps)
+        e1.record(runner.main)
+        e1.synchronize()
+        barrier()
+    mine_t = e0.elapsed_time(e1) / 1e3
+    dt = max_over_ranks(mine_t, dist)
+    launches = sum(L.lbmhd3_launch_count(h) for h in runner.h.values()) - launches0
+    my_planes = sum(runner.planes[s][1] - runner.planes[s][0] for s in mine)
+    per_rank = n * n * my_planes * args.steps / mine_t / 1e6
+    rates = [per_rank]
+    if dist:
+        t = torch.tensor([per_rank], dtype=torch.float64, device="cuda")
+        out = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(out, t)
+        rates = [float(x.item()) for x in out]
+    bpc = L.lbmhd3_bytes_per_cell(prec)
+    halo_total = decomp.halo_bytes_per_step3(n, n, n, k, les, bpc // 90)
+    value = n ** 3 * args.steps / dt / 1e6
+    runner.sync()
+    runner.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": DTYPES[prec].split(" ")[0], "data": "synthetic",
+            "config": {"workload": "3D decaying turbulence (D3Q27 + D3Q7), one lattice cut into z-slabs",
+                       "nx": n, "ny": n, "nz": n, "precision": prec, "les": les,
+                       "parallelism": f"z-slab decomposition: {k} slab(s) over {world} rank(s)",
+                       "l2": "state larger than L2, no flush"},
+            "decomp": {"slabs": k, "ranks": world, "overlap": not args.no_overlap,
+                       "halo_bytes_per_step": halo_total,
+                       "per_rank_MLUPS": rates,
+                       "hbm_frac_of_job": value * 1e6 * bpc / 1e9 / hbm / world},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def runner_halo(n, k, mine, les, vb):
     """Bytes the slabs `mine` receive per step."""
     from paper_1607_08675_gb300 import decomp
@@ -950,6 +1038,8 @@ def main():
     ap.add_argument("--study-n2", type=int, default=8192)
     ap.add_argument("--study-steps2", type=int, default=500)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--decomp3", action="store_true",
+                    help="one n3^3 3D lattice cut into z-slabs over the ranks (strong scaling)")
     ap.add_argument("--decomp", action="store_true",
                     help="one lattice cut into row slabs over the ranks (strong scaling)")
     ap.add_argument("--decomp-slabs", type=int, default=0,
@@ -964,6 +1054,8 @@ def main():
         precision_study(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.decomp3:
+        run_decomp3(args)
     elif args.decomp:
         run_decomp(args)
     else:

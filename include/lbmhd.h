@@ -420,6 +420,34 @@ int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
 int lbmhd3_sync(lbmhd3_t* h);
 int64_t lbmhd3_step_count(const lbmhd3_t* h);
 int64_t lbmhd3_launch_count(const lbmhd3_t* h);
+
+/* z-slab sharding of a 3D lattice (the step streams by a shift, Sec. 1.2,
+ * and collides locally, Sec. 3, so planes are advanced independently given
+ * their neighbours).
+ * lbmhd3_step_planes: planes z0 <= z < z1 of the next state (periodic pull)
+ * into the back buffer; the current state stays current.  Reads planes
+ * z0 - 1 .. z1 of the current state (z0 - 2 .. z1 + 1 with les 2, 3).
+ * Planes not computed before the commit keep the back buffer's older
+ * contents.  Asynchronous on the handle's stream.  EINVAL unless
+ * 0 <= z0 < z1 <= nz; ESTATE before init.
+ * lbmhd3_step_commit: the back buffer becomes the current state and the
+ * step counter advances (host only). */
+int lbmhd3_step_planes(lbmhd3_t* h, int z0, int z1);
+int lbmhd3_step_commit(lbmhd3_t* h);
+
+/* Halo messages of the 3D state: the planes selected by plane_mask (bit p
+ * = storage plane p of the 45) of z-plane z of the current state, gathered
+ * into (pack) or scattered from (unpack) buf: device memory of
+ * popcount(plane_mask) * nx * ny stored values in the storage format, plane
+ * after plane in increasing order, x fastest then y.  buf is caller-owned,
+ * aligned to the stored value size.  Enqueued on `stream` (cudaStream_t;
+ * NULL: the handle's stream).  A ghost plane below a slab needs the planes
+ * streaming upwards (c_z = +1: the 9 f_i with kz = 1 and g_{+z}); with les
+ * 2, 3 the nearer ghost plane also needs the c_z = 0 planes and the second
+ * ghost plane the upward ones.  EINVAL for NULL or misaligned buf, a plane
+ * outside the lattice or mask bits above 44; ESTATE (pack) before init. */
+int lbmhd3_pack_plane(lbmhd3_t* h, int z, uint64_t plane_mask, void* buf, void* stream);
+int lbmhd3_unpack_plane(lbmhd3_t* h, int z, uint64_t plane_mask, const void* buf, void* stream);
 /* Bytes a 3D step moves per node: 45 values read and written (0 for an
  * unsupported precision). */
 int lbmhd3_bytes_per_cell(int precision);

@@ -370,10 +370,16 @@ __device__ __forceinline__ void collide3(R (&d)[kQ], R (&g)[3 * kM], const Coll3
     }
 }
 
+// Lattice shape, plane stride, and the planes [zb, ze) a launch covers
+// (zb may be -1 and ze nz + 1 for a moments pass around a plane range;
+// planes wrap periodically).
 struct Geom3 {
     int nx, ny, nz;
     long long ps;
+    int zb, ze;
 };
+
+__host__ __device__ __forceinline__ int wrapz3(int z, int nz) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); }
 
 // The pull of one thread: V consecutive nodes along x of one (y, z) row;
 // every plane one aligned vector load, the x-shifted planes completed from
@@ -387,10 +393,10 @@ __device__ __forceinline__ void pull3(const typename Fmt3<P>::S* __restrict__ sr
     using S = typename Fmt3<P>::S;
     const int lane = threadIdx.x & 31;
     const unsigned nxv = (unsigned)(g.nx / V);
-    const unsigned row = tc / nxv;  // y + ny z
+    const unsigned row = tc / nxv;  // y + ny (z - zb)
     x0 = (int)(tc - row * nxv) * V;
     y = (int)(row % (unsigned)g.ny);
-    z = (int)(row / (unsigned)g.ny);
+    z = wrapz3(g.zb + (int)(row / (unsigned)g.ny), g.nz);
     const bool has_left = lane > 0 && x0 > 0;
     const bool has_right = lane < 31 && x0 + V < g.nx;
     const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;
@@ -513,9 +519,9 @@ __device__ __forceinline__ void step3_body_h(const unsigned short* __restrict__ 
     const bool live = t < total;
     const unsigned tc = live ? t : total - 1;
     const unsigned nxv = (unsigned)(g.nx / 2);
-    const unsigned row = tc / nxv;  // y + ny z
+    const unsigned row = tc / nxv;  // y + ny (z - zb)
     const int x0 = (int)(tc - row * nxv) * 2;
-    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    const int y = (int)(row % (unsigned)g.ny), z = wrapz3(g.zb + (int)(row / (unsigned)g.ny), g.nz);
     const bool has_left = lane > 0 && x0 > 0;
     const bool has_right = lane < 31 && x0 + 2 < g.nx;
     const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 || P == P_FF ? 1 : 3)
     const int seg = (int)blockIdx.x / (tiles_x * tiles_y);
     const int x0 = (tile % tiles_x) * kFX, y0 = (tile / tiles_x) * kFTY;
     const int tw = min(kFX, g.nx - x0), th = min(kFTY, g.ny - y0);
-    const int z0 = seg * seglen, z1 = min(z0 + seglen, g.nz);
+    const int z0 = g.zb + seg * seglen, z1 = min(z0 + seglen, g.ze);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int hw = tw + 2, hn = hw * (th + 2);
 
@@ -966,11 +972,23 @@ cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
                        const Coll3<typename Fmt3<P>::R>& c, int les, void* mom, cudaStream_t st) {
     using S = typename Fmt3<P>::S;
     using R = typename Fmt3<P>::R;
-    const unsigned total = (unsigned)((long long)g.nx / V * g.ny * g.nz);
+    const unsigned total = (unsigned)((long long)g.nx / V * g.ny * (g.ze - g.zb));
     const unsigned total_pad = (total + 31u) / 32u * 32u;
     const unsigned blocks = (total_pad + block - 1) / block;
     if (les == 2 || les == 3) {
-        mom3_kernel<P, V><<<blocks, block, 0, st>>>((const S*)src, (R*)mom, g, total, total_pad, c.i16);
+        // the fields of planes zb - 1 .. ze (all planes when that wraps round)
+        Geom3 gm = g;
+        if (g.ze - g.zb + 2 >= g.nz) {
+            gm.zb = 0;
+            gm.ze = g.nz;
+        } else {
+            gm.zb = g.zb - 1;
+            gm.ze = g.ze + 1;
+        }
+        const unsigned mtotal = (unsigned)((long long)g.nx / V * g.ny * (gm.ze - gm.zb));
+        const unsigned mpad = (mtotal + 31u) / 32u * 32u;
+        mom3_kernel<P, V><<<(mpad + block - 1) / block, block, 0, st>>>((const S*)src, (R*)mom, gm, mtotal,
+                                                                       mpad, c.i16);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (les == 2)
@@ -999,14 +1017,15 @@ cudaError_t launch_fused3(const void* src, void* dst, const Geom3& g,
     using R = typename Fmt3<P>::R;
     const int tiles_x = (g.nx + kFX - 1) / kFX, tiles_y = (g.ny + kFTY - 1) / kFTY;
     const long long tiles = (long long)tiles_x * tiles_y;
+    const int nzr = g.ze - g.zb;  // planes this launch computes
     int best_seg = 1;
     double best = -1.0;
     for (int waves = 1; waves <= 8; ++waves) {
         long long nseg = (waves * (long long)resident + tiles / 2) / tiles;
         if (nseg < 1) nseg = 1;
-        if (nseg > g.nz) nseg = g.nz;
-        const int seglen = (int)((g.nz + nseg - 1) / nseg);
-        nseg = (g.nz + seglen - 1) / seglen;
+        if (nseg > nzr) nseg = nzr;
+        const int seglen = (int)((nzr + nseg - 1) / nseg);
+        nseg = (nzr + seglen - 1) / seglen;
         const long long units = tiles * nseg;
         const long long slots = (units + resident - 1) / resident * resident;
         const double eff = (double)units / (double)slots * (double)seglen / (seglen + 1.0);
@@ -1015,7 +1034,7 @@ cudaError_t launch_fused3(const void* src, void* dst, const Geom3& g,
             best_seg = seglen;
         }
     }
-    const long long units = tiles * ((g.nz + best_seg - 1) / best_seg);
+    const long long units = tiles * ((nzr + best_seg - 1) / best_seg);
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)fused3_smem_floats() * sizeof(R);
     fused3_kernel<P, MODE><<<(unsigned)units, kFThreads, smem, st>>>((const S*)src, (S*)dst, g, tiles_x,
@@ -1128,23 +1147,71 @@ Coll3<R> coll3(const lbmhd_params& p) {
 
 long long nodes3(const lbmhd3_t* h) { return (long long)h->geom.nx * h->geom.ny * h->geom.nz; }
 
-cudaError_t one_step3(lbmhd3_t* h) {
+// Planes [z0, z1) of the next state into the back buffer.
+cudaError_t step3_planes(lbmhd3_t* h, int z0, int z1) {
     const void* src = h->buf[h->cur];
     void* dst = h->buf[1 - h->cur];
     const int les = h->p.les;
+    Geom3 g = h->geom;
+    g.zb = z0;
+    g.ze = z1;
     const cudaError_t e = by_prec3(h->p.precision, [&](auto tag) {
         constexpr int P = decltype(tag)::value;
         using R = typename Fmt3<P>::R;
         const Coll3<R> c = coll3<R>(h->p);
-        if (h->vec == 0) return launch_fused3_p<P>(les, src, dst, h->geom, c, h->fused_resident, h->stream);
-        return h->vec == 2 ? launch3_pv<P, 2>(h->block, src, dst, h->geom, c, les, h->mom, h->stream)
-                           : launch3_pv<P, 1>(h->block, src, dst, h->geom, c, les, h->mom, h->stream);
+        if (h->vec == 0) return launch_fused3_p<P>(les, src, dst, g, c, h->fused_resident, h->stream);
+        return h->vec == 2 ? launch3_pv<P, 2>(h->block, src, dst, g, c, les, h->mom, h->stream)
+                           : launch3_pv<P, 1>(h->block, src, dst, g, c, les, h->mom, h->stream);
     });
-    if (e == cudaSuccess) {
-        h->cur = 1 - h->cur;
-        h->launches += les >= 2 && h->vec != 0 ? 2 : 1;
-    }
+    if (e == cudaSuccess) h->launches += les >= 2 && h->vec != 0 ? 2 : 1;
     return e;
+}
+
+cudaError_t one_step3(lbmhd3_t* h) {
+    const cudaError_t e = step3_planes(h, 0, h->geom.nz);
+    if (e == cudaSuccess) h->cur = 1 - h->cur;
+    return e;
+}
+
+// Halo messages: the planes of a list, one z-plane each (nx ny stored
+// values), gathered from a state into buf or scattered from buf, as raw
+// values of the storage width.
+struct PlaneList3 {
+    int n;
+    int p[kP];
+};
+template <class T>
+__global__ void pack3_kernel(const T* __restrict__ st, long long ps, long long off, long long nxy,
+                             PlaneList3 pl, T* __restrict__ buf) {
+    const long long total = (long long)pl.n * nxy;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / nxy);
+        buf[i] = st[pl.p[k] * ps + off + (i - k * nxy)];
+    }
+}
+template <class T>
+__global__ void unpack3_kernel(T* __restrict__ st, long long ps, long long off, long long nxy,
+                               PlaneList3 pl, const T* __restrict__ buf) {
+    const long long total = (long long)pl.n * nxy;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / nxy);
+        st[pl.p[k] * ps + off + (i - k * nxy)] = buf[i];
+    }
+}
+
+template <class T>
+cudaError_t move3_planes(bool pack, void* st, long long ps, long long off, long long nxy,
+                         const PlaneList3& pl, void* buf, cudaStream_t stream) {
+    const long long total = (long long)pl.n * nxy;
+    if (total == 0) return cudaSuccess;
+    const unsigned blocks = grid3(total, 256);
+    if (pack)
+        pack3_kernel<T><<<blocks, 256, 0, stream>>>((const T*)st, ps, off, nxy, pl, (T*)buf);
+    else
+        unpack3_kernel<T><<<blocks, 256, 0, stream>>>((T*)st, ps, off, nxy, pl, (const T*)buf);
+    return cudaGetLastError();
 }
 
 // rho, u, B of the current state into seven FP64 device fields.
@@ -1197,6 +1264,8 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     h->geom.nz = nz;
     const long long n = (long long)nx * ny * nz;
     h->geom.ps = (n + 63) / 64 * 64;
+    h->geom.zb = 0;
+    h->geom.ze = nz;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) {
         delete h;
@@ -1321,6 +1390,60 @@ int lbmhd3_step(lbmhd3_t* h, int n) {
         ++h->steps;
     }
     return LBMHD_OK;
+}
+
+int lbmhd3_step_planes(lbmhd3_t* h, int z0, int z1) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!(0 <= z0 && z0 < z1 && z1 <= h->geom.nz))
+        return fail3(LBMHD_EINVAL, "planes: need 0 <= z0 < z1 <= nz");
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "lbmhd3_step_planes before lbmhd3_init");
+    LBMHD3_CK(h, step3_planes(h, z0, z1));
+    return LBMHD_OK;
+}
+
+int lbmhd3_step_commit(lbmhd3_t* h) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "lbmhd3_step_commit before lbmhd3_init");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+    return LBMHD_OK;
+}
+
+static int plane_move3(lbmhd3_t* h, bool pack, int z, uint64_t mask, void* buf, void* stream) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!buf) return fail3(LBMHD_EINVAL, "NULL buffer");
+    if (z < 0 || z >= h->geom.nz) return fail3(LBMHD_EINVAL, "plane outside the lattice");
+    if (mask >> kP) return fail3(LBMHD_EINVAL, "plane mask bits above 44");
+    const size_t vb = value3_bytes(h->p.precision);
+    if ((uintptr_t)buf % vb) return fail3(LBMHD_EINVAL, "buffer not aligned to the stored value size");
+    if (pack && !h->initialised) return fail3(LBMHD_ESTATE, "pack before lbmhd3_init");
+    PlaneList3 pl;
+    pl.n = 0;
+    for (int p = 0; p < kP; ++p)
+        if (mask >> p & 1) pl.p[pl.n++] = p;
+    const long long nxy = (long long)h->geom.nx * h->geom.ny;
+    cudaStream_t st = stream ? (cudaStream_t)stream : h->stream;
+    void* state = h->buf[h->cur];
+    cudaError_t e;
+    if (vb == 8)
+        e = move3_planes<unsigned long long>(pack, state, h->geom.ps, z * nxy, nxy, pl, buf, st);
+    else if (vb == 4)
+        e = move3_planes<unsigned>(pack, state, h->geom.ps, z * nxy, nxy, pl, buf, st);
+    else
+        e = move3_planes<unsigned short>(pack, state, h->geom.ps, z * nxy, nxy, pl, buf, st);
+    LBMHD3_CK(h, e);
+    return LBMHD_OK;
+}
+
+int lbmhd3_pack_plane(lbmhd3_t* h, int z, uint64_t mask, void* buf, void* stream) {
+    return plane_move3(h, true, z, mask, buf, stream);
+}
+
+int lbmhd3_unpack_plane(lbmhd3_t* h, int z, uint64_t mask, const void* buf, void* stream) {
+    return plane_move3(h, false, z, mask, const_cast<void*>(buf), stream);
 }
 
 int lbmhd3_moments(lbmhd3_t* h, double* out7) {

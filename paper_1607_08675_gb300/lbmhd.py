@@ -92,6 +92,10 @@ def lib() -> ctypes.CDLL:
                 "lbmhd3_step_count": (ctypes.c_int64, [h]),
                 "lbmhd3_launch_count": (ctypes.c_int64, [h]),
                 "lbmhd3_bytes_per_cell": (i, [i]),
+                "lbmhd3_step_planes": (i, [h, i, i]),
+                "lbmhd3_step_commit": (i, [h]),
+                "lbmhd3_pack_plane": (i, [h, i, ctypes.c_uint64, vp, vp]),
+                "lbmhd3_unpack_plane": (i, [h, i, ctypes.c_uint64, vp, vp]),
                 "lbmhd3_destroy": (None, [h]),
                 "lbmhd_step_commit": (i, [h]),
                 "lbmhd_pack_row": (i, [h, i, ctypes.c_uint, vp, vp]),
@@ -448,6 +452,24 @@ def lbmhd3_step_count(h: Handle3) -> int:
 
 def lbmhd3_launch_count(h: Handle3) -> int:
     return int(lib().lbmhd3_launch_count(h.ptr))
+
+
+def lbmhd3_step_planes(h: Handle3, z0: int, z1: int):
+    _check(lib().lbmhd3_step_planes(h.ptr, int(z0), int(z1)))
+
+
+def lbmhd3_step_commit(h: Handle3):
+    _check(lib().lbmhd3_step_commit(h.ptr))
+
+
+def lbmhd3_pack_plane(h: Handle3, z: int, plane_mask: int, buf, stream=None):
+    """Gather the masked planes of z-plane z into device memory buf (an
+    address or a tensor)."""
+    _check(lib().lbmhd3_pack_plane(h.ptr, int(z), int(plane_mask), _ptr(buf), _stream(stream)))
+
+
+def lbmhd3_unpack_plane(h: Handle3, z: int, plane_mask: int, buf, stream=None):
+    _check(lib().lbmhd3_unpack_plane(h.ptr, int(z), int(plane_mask), _ptr(buf), _stream(stream)))
 
 
 def lbmhd3_bytes_per_cell(precision) -> int:
