@@ -28,6 +28,7 @@
 // v = {0, 1, -1}.  Arithmetic in deviations d = f - w (g itself).
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -823,6 +824,18 @@ __global__ void __launch_bounds__(256) step3_kernel(const typename Fmt3<P>::S* _
         step3_body<P, V, MODE>(src, dst, g, t, total, c, mom);
 }
 
+// The FP32 two-node step without a closure, held to 168 registers: left to
+// itself ptxas takes 170, which the per-warp allocation rounds up to 176 per
+// thread, leaving room for two CTAs of 128 threads per SM instead of three
+// (measured 14.1K against 16.8K MLUPS at 256^3).
+__global__ void __maxnreg__(168)
+    step3f_kernel(const float* __restrict__ src, float* __restrict__ dst, Geom3 g, unsigned total,
+                  unsigned total_pad, Coll3<float> c) {
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total_pad; t += stride)
+        step3_body<P_FP32, 2, K3_LOCAL>(src, dst, g, t, total, c, nullptr);
+}
+
 // The FP16 two-node step without a closure, held to 128 registers (16 warps
 // per SM instead of 12; 8 bytes of spill).
 __global__ void __launch_bounds__(256, 2) step3h_kernel(const unsigned short* __restrict__ src,
@@ -1001,6 +1014,8 @@ cudaError_t launch3_pv(int block, const void* src, void* dst, const Geom3& g,
     }
     if constexpr (P == P_FP16_DEV && V == 2)
         step3h_kernel<<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total, total_pad, c);
+    else if constexpr (P == P_FP32 && V == 2)
+        step3f_kernel<<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total, total_pad, c);
     else
         step3_kernel<P, V, K3_LOCAL><<<blocks, block, 0, st>>>((const S*)src, (S*)dst, g, total,
                                                                total_pad, c, nullptr);
@@ -1175,42 +1190,43 @@ cudaError_t one_step3(lbmhd3_t* h) {
 
 // Halo messages: the planes of a list, one z-plane each (nx ny stored
 // values), gathered from a state into buf or scattered from buf, as raw
-// values of the storage width.
+// values of the storage width: grid row k copies plane pl.p[k], in 16-byte
+// words when a z-plane is a whole number of them (T = uint4), else in
+// values.
 struct PlaneList3 {
     int n;
     int p[kP];
 };
 template <class T>
-__global__ void pack3_kernel(const T* __restrict__ st, long long ps, long long off, long long nxy,
-                             PlaneList3 pl, T* __restrict__ buf) {
-    const long long total = (long long)pl.n * nxy;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / nxy);
-        buf[i] = st[pl.p[k] * ps + off + (i - k * nxy)];
-    }
-}
-template <class T>
-__global__ void unpack3_kernel(T* __restrict__ st, long long ps, long long off, long long nxy,
-                               PlaneList3 pl, const T* __restrict__ buf) {
-    const long long total = (long long)pl.n * nxy;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / nxy);
-        st[pl.p[k] * ps + off + (i - k * nxy)] = buf[i];
+__global__ void __launch_bounds__(256) move3_kernel(bool pack, T* __restrict__ st, long long ps_w,
+                                                    long long off_w, int nw, PlaneList3 pl,
+                                                    T* __restrict__ buf) {
+    const int k = blockIdx.y;
+    T* s = st + pl.p[k] * ps_w + off_w;
+    T* b = buf + (long long)k * nw;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x) {
+        if (pack)
+            b[i] = s[i];
+        else
+            s[i] = b[i];
     }
 }
 
 template <class T>
 cudaError_t move3_planes(bool pack, void* st, long long ps, long long off, long long nxy,
                          const PlaneList3& pl, void* buf, cudaStream_t stream) {
-    const long long total = (long long)pl.n * nxy;
-    if (total == 0) return cudaSuccess;
-    const unsigned blocks = grid3(total, 256);
-    if (pack)
-        pack3_kernel<T><<<blocks, 256, 0, stream>>>((const T*)st, ps, off, nxy, pl, (T*)buf);
-    else
-        unpack3_kernel<T><<<blocks, 256, 0, stream>>>((T*)st, ps, off, nxy, pl, (const T*)buf);
+    if (pl.n == 0 || nxy == 0) return cudaSuccess;
+    const bool wide = (nxy * (long long)sizeof(T)) % 16 == 0 && (ps * (long long)sizeof(T)) % 16 == 0 &&
+                      (uintptr_t)st % 16 == 0 && (uintptr_t)buf % 16 == 0;
+    if (wide) {
+        const long long r = 16 / (long long)sizeof(T);  // values per word
+        const int nw = (int)(nxy / r);
+        const dim3 grid((unsigned)std::min<long long>((nw + 255) / 256, 1024), (unsigned)pl.n);
+        move3_kernel<uint4><<<grid, 256, 0, stream>>>(pack, (uint4*)st, ps / r, off / r, nw, pl, (uint4*)buf);
+    } else {
+        const dim3 grid((unsigned)std::min<long long>((nxy + 255) / 256, 1024), (unsigned)pl.n);
+        move3_kernel<T><<<grid, 256, 0, stream>>>(pack, (T*)st, ps, off, (int)nxy, pl, (T*)buf);
+    }
     return cudaGetLastError();
 }
 
