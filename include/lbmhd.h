@@ -399,6 +399,29 @@ int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* 
                 const double* uz, const double* bx, const double* by, const double* bz);
 /* n fused stream-collide steps, asynchronous on the handle's stream. */
 int lbmhd3_step(lbmhd3_t* h, int n);
+/* As lbmhd3_init, from seven device fields of nx*ny*nz doubles; enqueued on
+ * the handle's stream (no check of rho). */
+int lbmhd3_init_device(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
+                       const double* uz, const double* bx, const double* by, const double* bz);
+/* As lbmhd3_moments, into seven device fields; enqueued, does not
+ * synchronise. */
+int lbmhd3_moments_device(lbmhd3_t* h, double* rho, double* ux, double* uy, double* uz,
+                          double* bx, double* by, double* bz);
+/* Replace the state with host FP64 planes (layout as lbmhd3_get_state),
+ * encoded to the storage format; the step counter is left unchanged.  With
+ * lbmhd3_get_state this is checkpoint / resume, bit for bit for FP64, FP32
+ * and FP16 storage (FF pairs are rounded to FP64 on the way out; the raw
+ * pair below is exact for every format).  Synchronises. */
+int lbmhd3_set_state(lbmhd3_t* h, const double* state);
+/* The stored state in its own format: a host buffer of bytes = 45 * nodes
+ * * value size (8 FP64 and FF, 4 FP32, 2 FP16), plane p at byte offset
+ * p * nodes * value size, node (x, y, z) at (z ny + y) nx + x.  Values: FP64
+ * / FP32 populations; FP16 binary16 deviations f - w (g itself) times
+ * fp16_scale; FF (hi, lo) FP32 pairs of the deviations.  Caller-owned;
+ * synchronises.  EINVAL for NULL or a wrong byte count; ESTATE (get) before
+ * init.  set leaves the step counter unchanged. */
+int lbmhd3_get_state_raw(lbmhd3_t* h, void* state, size_t bytes);
+int lbmhd3_set_state_raw(lbmhd3_t* h, const void* state, size_t bytes);
 /* rho, ux, uy, uz, bx, by, bz into out7 (host, 7 * nx*ny*nz doubles, field
  * after field); synchronises. */
 int lbmhd3_moments(lbmhd3_t* h, double* out7);

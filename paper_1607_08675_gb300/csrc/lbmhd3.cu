@@ -847,14 +847,19 @@ __global__ void __launch_bounds__(256, 2) step3h_kernel(const unsigned short* __
         step3_body_h<K3_LOCAL>(src, dst, g, t, total, c, nullptr);
 }
 
+// Seven FP64 device fields: rho, ux, uy, uz, Bx, By, Bz.
+struct Fields7 {
+    double* f[7];
+};
+
 // Equilibrium initialisation from seven FP64 device fields.
 template <int P>
-__global__ void init3_kernel(const double* __restrict__ f7, long long n,
-                             typename Fmt3<P>::S* __restrict__ st, long long ps, double s16) {
+__global__ void init3_kernel(Fields7 in, long long n, typename Fmt3<P>::S* __restrict__ st,
+                             long long ps, double s16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double rho = f7[i], u[3] = {f7[n + i], f7[2 * n + i], f7[3 * n + i]},
-                     B[3] = {f7[4 * n + i], f7[5 * n + i], f7[6 * n + i]};
+        const double rho = in.f[0][i], u[3] = {in.f[1][i], in.f[2][i], in.f[3][i]},
+                     B[3] = {in.f[4][i], in.f[5][i], in.f[6][i]};
         const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
         const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
@@ -882,7 +887,7 @@ __global__ void init3_kernel(const double* __restrict__ f7, long long n,
 // rho, u (3), B (3) of the stored state into seven FP64 fields.
 template <int P>
 __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps,
-                                long long n, double* __restrict__ m7, double i16) {
+                                long long n, Fields7 out, double i16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
@@ -898,12 +903,22 @@ __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long
         for (int q = 0; q < kM; ++q)
 #pragma unroll
             for (int b = 0; b < 3; ++b) B[b] += Fmt3<P>::to_f(st[(kQ + 3 * q + b) * ps + i], kQ + 3 * q + b, i16);
-        m7[i] = rho;
+        out.f[0][i] = rho;
         for (int a = 0; a < 3; ++a) {
-            m7[(1 + a) * n + i] = j[a] / rho;
-            m7[(4 + a) * n + i] = B[a];
+            out.f[1 + a][i] = j[a] / rho;
+            out.f[4 + a][i] = B[a];
         }
     }
+}
+
+// 45 FP64 planes of n encoded into the storage format.
+template <int P>
+__global__ void set3_kernel(const double* __restrict__ in, long long n,
+                            typename Fmt3<P>::S* __restrict__ st, long long ps, double s16) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int p = 0; p < kP; ++p) st[p * ps + i] = Fmt3<P>::from_f(in[p * n + i], p, s16);
 }
 
 // The stored state decoded to 45 FP64 planes of n.
@@ -1230,14 +1245,35 @@ cudaError_t move3_planes(bool pack, void* st, long long ps, long long off, long 
     return cudaGetLastError();
 }
 
+Fields7 contiguous7(double* base, long long n) {
+    Fields7 f;
+    for (int q = 0; q < 7; ++q) f.f[q] = base + q * n;
+    return f;
+}
+
 // rho, u, B of the current state into seven FP64 device fields.
-cudaError_t moments3_into(lbmhd3_t* h, double* m7) {
+cudaError_t moments3_fields(lbmhd3_t* h, const Fields7& out) {
     const long long n = (long long)h->geom.nx * h->geom.ny * h->geom.nz;
     return by_prec3(h->p.precision, [&](auto tag) {
         constexpr int P = decltype(tag)::value;
         using S = typename Fmt3<P>::S;
         moments3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>((const S*)h->buf[h->cur], h->geom.ps, n,
-                                                                  m7, 1.0 / h->p.fp16_scale);
+                                                                  out, 1.0 / h->p.fp16_scale);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t moments3_into(lbmhd3_t* h, double* m7) {
+    return moments3_fields(h, contiguous7(m7, (long long)h->geom.nx * h->geom.ny * h->geom.nz));
+}
+
+// Equilibrium initialisation of the current buffer from device fields.
+cudaError_t init3_fields(lbmhd3_t* h, const Fields7& in) {
+    const long long n = (long long)h->geom.nx * h->geom.ny * h->geom.nz;
+    return by_prec3(h->p.precision, [&](auto tag) {
+        constexpr int P = decltype(tag)::value;
+        init3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>(in, n, (typename Fmt3<P>::S*)h->buf[h->cur],
+                                                               h->geom.ps, h->p.fp16_scale);
         return cudaGetLastError();
     });
 }
@@ -1383,17 +1419,90 @@ int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* 
     for (int i = 0; i < 7; ++i)
         LBMHD3_CK(h, cudaMemcpyAsync(tmp + i * n, f[i], n * sizeof(double), cudaMemcpyHostToDevice,
                                      h->stream));
+    LBMHD3_CK(h, init3_fields(h, contiguous7(tmp, n)));
+    LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    h->steps = 0;
+    return LBMHD_OK;
+}
+
+int lbmhd3_init_device(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
+                       const double* uz, const double* bx, const double* by, const double* bz) {
+    int rc = check3(h);
+    if (rc) return rc;
+    const double* f[7] = {rho, ux, uy, uz, bx, by, bz};
+    Fields7 in;
+    for (int i = 0; i < 7; ++i) {
+        if (!f[i]) return fail3(LBMHD_EINVAL, "NULL field");
+        in.f[i] = const_cast<double*>(f[i]);
+    }
+    LBMHD3_CK(h, init3_fields(h, in));
+    h->initialised = true;
+    h->steps = 0;
+    return LBMHD_OK;
+}
+
+int lbmhd3_moments_device(lbmhd3_t* h, double* rho, double* ux, double* uy, double* uz,
+                          double* bx, double* by, double* bz) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!h->initialised) return fail3(LBMHD_ESTATE, "moments before lbmhd3_init");
+    double* f[7] = {rho, ux, uy, uz, bx, by, bz};
+    Fields7 out;
+    for (int i = 0; i < 7; ++i) {
+        if (!f[i]) return fail3(LBMHD_EINVAL, "NULL field");
+        out.f[i] = f[i];
+    }
+    LBMHD3_CK(h, moments3_fields(h, out));
+    return LBMHD_OK;
+}
+
+int lbmhd3_set_state(lbmhd3_t* h, const double* state) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!state) return fail3(LBMHD_EINVAL, "NULL state");
+    const long long n = nodes3(h);
+    double* tmp = nullptr;
+    LBMHD3_CK(h, cudaMallocAsync((void**)&tmp, (size_t)kP * n * sizeof(double), h->stream));
+    LBMHD3_CK(h, cudaMemcpyAsync(tmp, state, (size_t)kP * n * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream));
     LBMHD3_CK(h, by_prec3(h->p.precision, [&](auto tag) {
                   constexpr int P = decltype(tag)::value;
-                  init3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>(
+                  set3_kernel<P><<<grid3(n, 256), 256, 0, h->stream>>>(
                       tmp, n, (typename Fmt3<P>::S*)h->buf[h->cur], h->geom.ps, h->p.fp16_scale);
                   return cudaGetLastError();
               }));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
-    h->steps = 0;
     return LBMHD_OK;
+}
+
+static int raw3(lbmhd3_t* h, bool get, void* state, size_t bytes) {
+    int rc = check3(h);
+    if (rc) return rc;
+    if (!state) return fail3(LBMHD_EINVAL, "NULL state");
+    const size_t vb = value3_bytes(h->p.precision);
+    const size_t row = (size_t)nodes3(h) * vb;
+    if (bytes != (size_t)kP * row) return fail3(LBMHD_EINVAL, "byte count is not 45 * nodes * value size");
+    if (get && !h->initialised) return fail3(LBMHD_ESTATE, "get_state_raw before lbmhd3_init");
+    const size_t pitch = (size_t)h->geom.ps * vb;
+    if (get)
+        LBMHD3_CK(h, cudaMemcpy2DAsync(state, row, h->buf[h->cur], pitch, row, kP, cudaMemcpyDeviceToHost,
+                                       h->stream));
+    else
+        LBMHD3_CK(h, cudaMemcpy2DAsync(h->buf[h->cur], pitch, state, row, row, kP, cudaMemcpyHostToDevice,
+                                       h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    if (!get) h->initialised = true;
+    return LBMHD_OK;
+}
+
+int lbmhd3_get_state_raw(lbmhd3_t* h, void* state, size_t bytes) { return raw3(h, true, state, bytes); }
+
+int lbmhd3_set_state_raw(lbmhd3_t* h, const void* state, size_t bytes) {
+    return raw3(h, false, const_cast<void*>(state), bytes);
 }
 
 int lbmhd3_step(lbmhd3_t* h, int n) {

@@ -93,6 +93,11 @@ def lib() -> ctypes.CDLL:
                 "lbmhd3_launch_count": (ctypes.c_int64, [h]),
                 "lbmhd3_bytes_per_cell": (i, [i]),
                 "lbmhd3_step_planes": (i, [h, i, i]),
+                "lbmhd3_init_device": (i, [h, vp, vp, vp, vp, vp, vp, vp]),
+                "lbmhd3_moments_device": (i, [h, vp, vp, vp, vp, vp, vp, vp]),
+                "lbmhd3_set_state": (i, [h, vp]),
+                "lbmhd3_get_state_raw": (i, [h, vp, ctypes.c_size_t]),
+                "lbmhd3_set_state_raw": (i, [h, vp, ctypes.c_size_t]),
                 "lbmhd3_step_commit": (i, [h]),
                 "lbmhd3_pack_plane": (i, [h, i, ctypes.c_uint64, vp, vp]),
                 "lbmhd3_unpack_plane": (i, [h, i, ctypes.c_uint64, vp, vp]),
@@ -395,6 +400,10 @@ class Handle3:
     def shape(self):
         return (self.nz, self.ny, self.nx)
 
+    @property
+    def precision(self) -> int:
+        return int(self.params.precision)
+
 
 def lbmhd3_create(nx: int, ny: int, nz: int, params: Params | None = None) -> Handle3:
     params = params if params is not None else lbmhd_params_default()
@@ -452,6 +461,38 @@ def lbmhd3_step_count(h: Handle3) -> int:
 
 def lbmhd3_launch_count(h: Handle3) -> int:
     return int(lib().lbmhd3_launch_count(h.ptr))
+
+
+def lbmhd3_init_device(h: Handle3, rho, ux, uy, uz, bx, by, bz):
+    """Initialise from seven contiguous float64 CUDA tensors of shape
+    (nz, ny, nx)."""
+    _check(lib().lbmhd3_init_device(h.ptr, *[_dev(t, h.shape) for t in (rho, ux, uy, uz, bx, by, bz)]))
+
+
+def lbmhd3_moments_device(h: Handle3, rho, ux, uy, uz, bx, by, bz):
+    _check(lib().lbmhd3_moments_device(h.ptr, *[_dev(t, h.shape) for t in (rho, ux, uy, uz, bx, by, bz)]))
+
+
+def lbmhd3_set_state(h: Handle3, state):
+    st = _host(state, (45,) + h.shape)
+    _check(lib().lbmhd3_set_state(h.ptr, st.ctypes.data_as(ctypes.c_void_p)))
+
+
+def lbmhd3_get_state_raw(h: Handle3) -> np.ndarray:
+    """The stored state in its own format, shape (45, nz, ny, nx) (FF: with a
+    trailing 2 for the (hi, lo) pair)."""
+    dt, tail = RAW_DTYPES[h.precision]
+    st = np.empty((45,) + h.shape + tail, dtype=dt)
+    _check(lib().lbmhd3_get_state_raw(h.ptr, st.ctypes.data_as(ctypes.c_void_p), st.nbytes))
+    return st
+
+
+def lbmhd3_set_state_raw(h: Handle3, state):
+    dt, tail = RAW_DTYPES[h.precision]
+    st = np.ascontiguousarray(state, dtype=dt)
+    if st.shape != (45,) + h.shape + tail:
+        raise ValueError(f"expected shape {(45,) + h.shape + tail}")
+    _check(lib().lbmhd3_set_state_raw(h.ptr, st.ctypes.data_as(ctypes.c_void_p), st.nbytes))
 
 
 def lbmhd3_step_planes(h: Handle3, z0: int, z1: int):

@@ -265,3 +265,48 @@ def test_refused_configurations(L):
     h = L.lbmhd3_create(6, 4, 4, L.lbmhd_params_default(precision="fp32", les=2))
     assert L.lbmhd3_get_launch(h) == (0, 4)  # FP32 closures default to the fused kernel
     L.lbmhd3_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16_dev", "ff"])
+def test_checkpoint_resume_and_device_io(L, prec):
+    """Checkpoint / resume: a run interrupted after 17 steps, its state read
+    out and written into a fresh handle, continues bit for bit as the
+    uninterrupted run -- through the raw stored values for every format,
+    through FP64 planes for FP64, FP32 and FP16 storage.  Initialisation
+    and moments through device fields equal the host-array calls."""
+    import torch
+
+    shape = (18, 10, 7)
+    nx, ny, nz = shape
+    fields = inputs.turbulence3d(*shape, kmin=1, kmax=3, rms=0.05, seed=12)
+    kw = dict(KW, les=1, precision=prec)
+    ref = gpu3(L, fields, 30, **kw)[1]
+    a = L.lbmhd3_create(*shape, L.lbmhd_params_default(**kw))
+    L.lbmhd3_init(a, *fields)
+    L.lbmhd3_step(a, 17)
+    raw, fp = L.lbmhd3_get_state_raw(a), L.lbmhd3_get_state(a)
+    L.lbmhd3_destroy(a)
+    routes = [("raw", raw)] + ([("fp64", fp)] if prec != "ff" else [])
+    for name, st in routes:
+        b = L.lbmhd3_create(*shape, L.lbmhd_params_default(**kw))
+        (L.lbmhd3_set_state_raw if name == "raw" else L.lbmhd3_set_state)(b, st)
+        L.lbmhd3_step(b, 13)
+        assert np.array_equal(L.lbmhd3_get_state(b), ref), name
+        L.lbmhd3_destroy(b)
+    # device fields
+    dev = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in fields]
+    c = L.lbmhd3_create(*shape, L.lbmhd_params_default(**kw))
+    L.lbmhd3_init_device(c, *dev)
+    L.lbmhd3_step(c, 30)
+    out = [torch.empty_like(dev[0]) for _ in range(7)]
+    L.lbmhd3_moments_device(c, *out)
+    torch.cuda.synchronize()
+    assert np.array_equal(L.lbmhd3_get_state(c), ref)
+    host = L.lbmhd3_moments(c)
+    for q in range(7):
+        assert np.array_equal(out[q].cpu().numpy(), host[q])
+    with pytest.raises(ValueError):
+        L.lbmhd3_set_state_raw(c, raw[:-1])
+    import ctypes
+    assert L.lib().lbmhd3_set_state_raw(c.ptr, raw.ctypes.data_as(ctypes.c_void_p), raw.nbytes - 1) == -1
+    L.lbmhd3_destroy(c)
