@@ -387,7 +387,11 @@ int lbmhd_adjoint_release(lbmhd_t* h);
  * closure's relaxation times (Eqs. CHClosureV/B with 3D strain and curl). */
 typedef struct lbmhd3_t lbmhd3_t;
 
-/* Uses precision (FP64, FP32, FP16_DEV with fp16_scale, or FF), tau_nu, tau_eta, C_S, delta, les (0 off,
+/* Uses precision (FP64, FP32, FP16_DEV with fp16_scale, or FF), check_finite_every (every k steps
+ * the rest population f_0 and the first magnetic plane of every node are
+ * tested; a non-finite value is seen at most one step after it appears and
+ * reported as ENONFINITE by the next lbmhd3_sync, moments, get_state or
+ * diagnostics call until the next init or state write), tau_nu, tau_eta, C_S, delta, les (0 off,
  * 1 local rates, 2 filtered equilibria, 3 cross-helicity closure) and stream
  * of p.  Allocates two state buffers, and for les 2, 3 seven field planes.
  * EINVAL for other precisions or closures, tau <= 1/2, more than 2^30

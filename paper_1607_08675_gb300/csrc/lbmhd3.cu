@@ -911,6 +911,20 @@ __global__ void moments3_kernel(const typename Fmt3<P>::S* __restrict__ st, long
     }
 }
 
+// Non-finite check: the rest population f_0 and the first magnetic plane
+// of every node.  A non-finite value in any population of a node makes
+// every post-collision population of the nodes that pull it non-finite,
+// so a check after each step sees it at most one step after it appears.
+template <int P>
+__global__ void finite3_kernel(const typename Fmt3<P>::S* __restrict__ st, long long ps, long long n,
+                               double i16, int* __restrict__ flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double a = Fmt3<P>::to_f(st[i], 0, i16), b = Fmt3<P>::to_f(st[kQ * ps + i], kQ, i16);
+        if (!isfinite(a) || !isfinite(b)) atomicOr(flag, 1);
+    }
+}
+
 // 45 FP64 planes of n encoded into the storage format.
 template <int P>
 __global__ void set3_kernel(const double* __restrict__ in, long long n,
@@ -1116,6 +1130,7 @@ struct lbmhd3_t {
     int fused_resident;  // resident fused CTAs on the device
     int64_t steps, launches;
     void* mom;       // field planes of the gradient closures (les 2, 3)
+    int* d_flag;     // bit 0: a non-finite value seen (check_finite_every)
     double* d_m7;    // moment fields for the diagnostics (allocated on first use)
     double* d_rows;  // diagnostics partial rows
     double* d_out;
@@ -1155,6 +1170,16 @@ cudaError_t by_prec3(int prec, F f) {
     if (prec == LBMHD_FP16_DEV) return f(std::integral_constant<int, P_FP16_DEV>{});
     if (prec == LBMHD_FF) return f(std::integral_constant<int, P_FF>{});
     return cudaErrorInvalidValue;
+}
+
+// The pending non-finite report: ENONFINITE once the flag is set (until the
+// next init or state write).  Synchronises.
+int read_flag3(lbmhd3_t* h) {
+    int flag = 0;
+    LBMHD3_CK(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    if (flag & 1) return fail3(LBMHD_ENONFINITE, "non-finite value detected in the 3D state");
+    return LBMHD_OK;
 }
 
 template <class R>
@@ -1307,6 +1332,7 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
         return fail3(LBMHD_EINVAL, "tau_nu and tau_eta must be finite and > 1/2");
     if (!(p->C_S >= 0.0) || !(p->C_S < 1e6) || !(p->delta > 0.0) || !(p->delta < 1e6))
         return fail3(LBMHD_EINVAL, "C_S must be >= 0 and delta > 0, both finite");
+    if (p->check_finite_every < 0) return fail3(LBMHD_EINVAL, "check_finite_every must be >= 0");
     lbmhd3_t* h = new (std::nothrow) lbmhd3_t();
     if (!h) return fail3(LBMHD_ENOMEM, "host allocation failed");
     std::memset((void*)h, 0, sizeof(*h));
@@ -1337,9 +1363,9 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
     // field planes in the arithmetic type: FP64, or FP32 for the FP32 and FP16 formats
     const size_t mbytes =
         p->les >= 2 ? (size_t)7 * h->geom.ps * (p->precision == LBMHD_FP64 || p->precision == LBMHD_FF ? 8 : 4) : 0;
-    void** bufs[3] = {&h->buf[0], &h->buf[1], &h->mom};
-    const size_t sizes[3] = {bytes, bytes, mbytes};
-    for (int b = 0; b < 3; ++b) {
+    void** bufs[4] = {&h->buf[0], &h->buf[1], &h->mom, (void**)&h->d_flag};
+    const size_t sizes[4] = {bytes, bytes, mbytes, sizeof(int)};
+    for (int b = 0; b < 4; ++b) {
         if (!sizes[b]) continue;
         e = cudaMalloc(bufs[b], sizes[b]);
         if (e != cudaSuccess) {
@@ -1420,6 +1446,7 @@ int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* 
         LBMHD3_CK(h, cudaMemcpyAsync(tmp + i * n, f[i], n * sizeof(double), cudaMemcpyHostToDevice,
                                      h->stream));
     LBMHD3_CK(h, init3_fields(h, contiguous7(tmp, n)));
+    LBMHD3_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
@@ -1438,6 +1465,7 @@ int lbmhd3_init_device(lbmhd3_t* h, const double* rho, const double* ux, const d
         in.f[i] = const_cast<double*>(f[i]);
     }
     LBMHD3_CK(h, init3_fields(h, in));
+    LBMHD3_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
     h->initialised = true;
     h->steps = 0;
     return LBMHD_OK;
@@ -1474,6 +1502,7 @@ int lbmhd3_set_state(lbmhd3_t* h, const double* state) {
                   return cudaGetLastError();
               }));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
+    LBMHD3_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     h->initialised = true;
     return LBMHD_OK;
@@ -1491,9 +1520,11 @@ static int raw3(lbmhd3_t* h, bool get, void* state, size_t bytes) {
     if (get)
         LBMHD3_CK(h, cudaMemcpy2DAsync(state, row, h->buf[h->cur], pitch, row, kP, cudaMemcpyDeviceToHost,
                                        h->stream));
-    else
+    else {
         LBMHD3_CK(h, cudaMemcpy2DAsync(h->buf[h->cur], pitch, state, row, row, kP, cudaMemcpyHostToDevice,
                                        h->stream));
+        LBMHD3_CK(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    }
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     if (!get) h->initialised = true;
     return LBMHD_OK;
@@ -1510,9 +1541,19 @@ int lbmhd3_step(lbmhd3_t* h, int n) {
     if (rc) return rc;
     if (n < 0) return fail3(LBMHD_EINVAL, "n must be >= 0");
     if (!h->initialised) return fail3(LBMHD_ESTATE, "lbmhd3_step before lbmhd3_init");
+    const int every = h->p.check_finite_every;
+    const long long nn = nodes3(h);
     for (int s = 0; s < n; ++s) {
         LBMHD3_CK(h, one_step3(h));
         ++h->steps;
+        if (every > 0 && h->steps % every == 0)
+            LBMHD3_CK(h, by_prec3(h->p.precision, [&](auto tag) {
+                          constexpr int P = decltype(tag)::value;
+                          finite3_kernel<P><<<grid3(nn, 256), 256, 0, h->stream>>>(
+                              (const typename Fmt3<P>::S*)h->buf[h->cur], h->geom.ps, nn,
+                              1.0 / h->p.fp16_scale, h->d_flag);
+                          return cudaGetLastError();
+                      }));
     }
     return LBMHD_OK;
 }
@@ -1583,7 +1624,7 @@ int lbmhd3_moments(lbmhd3_t* h, double* out7) {
     LBMHD3_CK(h, cudaMemcpyAsync(out7, tmp, 7 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
-    return LBMHD_OK;
+    return read_flag3(h);  // a pending non-finite report
 }
 
 int lbmhd3_get_state(lbmhd3_t* h, double* out) {
@@ -1604,7 +1645,7 @@ int lbmhd3_get_state(lbmhd3_t* h, double* out) {
                                  h->stream));
     LBMHD3_CK(h, cudaFreeAsync(tmp, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
-    return LBMHD_OK;
+    return read_flag3(h);  // a pending non-finite report
 }
 
 int lbmhd3_diagnostics(lbmhd3_t* h, double* out12) {
@@ -1628,14 +1669,14 @@ int lbmhd3_diagnostics(lbmhd3_t* h, double* out12) {
     LBMHD3_CK(h, cudaMemcpyAsync(out12, h->d_out, 12 * sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
-    return LBMHD_OK;
+    return read_flag3(h);  // a pending non-finite report
 }
 
 int lbmhd3_sync(lbmhd3_t* h) {
     int rc = check3(h);
     if (rc) return rc;
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
-    return LBMHD_OK;
+    return h->initialised ? read_flag3(h) : LBMHD_OK;
 }
 
 int64_t lbmhd3_step_count(const lbmhd3_t* h) { return h ? h->steps : 0; }
@@ -1648,6 +1689,7 @@ void lbmhd3_destroy(lbmhd3_t* h) {
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->mom);
+    cudaFree(h->d_flag);
     cudaFree(h->d_m7);
     cudaFree(h->d_rows);
     cudaFree(h->d_out);

@@ -310,3 +310,35 @@ def test_checkpoint_resume_and_device_io(L, prec):
     import ctypes
     assert L.lib().lbmhd3_set_state_raw(c.ptr, raw.ctypes.data_as(ctypes.c_void_p), raw.nbytes - 1) == -1
     L.lbmhd3_destroy(c)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16_dev"])
+def test_non_finite_detection(L, prec):
+    """check_finite_every = 1: a clean run is unchanged and reports nothing;
+    a NaN written into one population of one node (a host-side injection)
+    is reported as ENONFINITE by the next synchronising call; a new init
+    clears the report."""
+    shape = (16, 8, 6)
+    fields = inputs.turbulence3d(*shape, seed=13)
+    kw = dict(KW, les=1, precision=prec)
+    ref = gpu3(L, fields, 12, **kw)[1]
+    h = L.lbmhd3_create(*shape, L.lbmhd_params_default(check_finite_every=1, **kw))
+    L.lbmhd3_init(h, *fields)
+    L.lbmhd3_step(h, 12)
+    L.lbmhd3_sync(h)
+    assert np.array_equal(L.lbmhd3_get_state(h), ref)
+    st = L.lbmhd3_get_state(h)
+    st[13, 3, 4, 5] = np.nan
+    L.lbmhd3_set_state(h, st)
+    L.lbmhd3_step(h, 2)
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd3_sync(h)
+    assert "non-finite" in str(e.value)
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd3_moments(h)
+    L.lbmhd3_init(h, *fields)
+    L.lbmhd3_step(h, 2)
+    L.lbmhd3_sync(h)
+    L.lbmhd3_destroy(h)
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd3_create(*shape, L.lbmhd_params_default(check_finite_every=-1, **kw))
