@@ -143,7 +143,10 @@ int lbmhd_create(int nx, int ny, const lbmhd_params* p, lbmhd_t** out);
 int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                const double* bx, const double* by);
 
-/* As lbmhd_init, from device fields; enqueued on the handle's stream. */
+/* As lbmhd_init, from device fields; enqueued on the handle's stream.  The
+ * fields are read in that stream's order: the caller completes them first
+ * (produces them on the handle's stream, or synchronises), and keeps them
+ * until the handle's stream has passed the call. */
 int lbmhd_init_device(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                       const double* bx, const double* by);
 
@@ -404,7 +407,10 @@ int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* 
 /* n fused stream-collide steps, asynchronous on the handle's stream. */
 int lbmhd3_step(lbmhd3_t* h, int n);
 /* As lbmhd3_init, from seven device fields of nx*ny*nz doubles; enqueued on
- * the handle's stream (no check of rho). */
+ * the handle's stream (no check of rho).  The fields are read in that
+ * stream's order: the caller completes them first (produces them on the
+ * handle's stream, or synchronises), and keeps them until the handle's
+ * stream has passed the call. */
 int lbmhd3_init_device(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
                        const double* uz, const double* bx, const double* by, const double* bz);
 /* As lbmhd3_moments, into seven device fields; enqueued, does not

@@ -295,6 +295,7 @@ def test_checkpoint_resume_and_device_io(L, prec):
         L.lbmhd3_destroy(b)
     # device fields
     dev = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in fields]
+    torch.cuda.synchronize()  # complete before the handle's stream reads them
     c = L.lbmhd3_create(*shape, L.lbmhd_params_default(**kw))
     L.lbmhd3_init_device(c, *dev)
     L.lbmhd3_step(c, 30)

@@ -42,6 +42,7 @@ def test_maximum_size_lattice_sampled(orc, nx, ny):
         jj = torch.arange(ny, dtype=torch.float64, device=dev)[:, None]
         ii = torch.arange(nx, dtype=torch.float64, device=dev)[None, :]
         f = [t.expand(ny, nx).contiguous() for t in fields_at(ii, jj, nx, ny, torch)]
+        torch.cuda.synchronize()  # the fields are complete before the handle's stream reads them
         mass0 = float(f[0].sum())
         L.lbmhd_init_device(h, *f)
         L.lbmhd_sync(h)
