@@ -103,6 +103,8 @@ template <> struct Fmt3<P_FP64> {
     static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest3<R>(p); }
     static __device__ __forceinline__ double to_f(S v, int, double) { return v; }
     static __device__ __forceinline__ S from_f(double f, int, double) { return f; }
+    // from the population f and its deviation d = f - w_p, both in FP64
+    static __device__ __forceinline__ S from_fd(double f, double, int, double) { return f; }
 };
 template <> struct Fmt3<P_FP32> {
     using S = float;
@@ -111,6 +113,7 @@ template <> struct Fmt3<P_FP32> {
     static __device__ __forceinline__ S enc(R d, int p, float) { return d + plane_rest3<R>(p); }
     static __device__ __forceinline__ double to_f(S v, int, double) { return (double)v; }
     static __device__ __forceinline__ S from_f(double f, int, double) { return (float)f; }
+    static __device__ __forceinline__ S from_fd(double f, double, int, double) { return (float)f; }
 };
 // double-word deviations (hi, lo) of f - w_p (g itself), double-word
 // arithmetic (the FP32 pipes)
@@ -125,6 +128,10 @@ template <> struct Fmt3<P_FF> {
     static __device__ __forceinline__ S from_f(double f, int p, double) {
         const ff d(f - plane_rest3<double>(p));
         return make_float2(d.hi, d.lo);
+    }
+    static __device__ __forceinline__ S from_fd(double, double d, int, double) {
+        const ff v(d);
+        return make_float2(v.hi, v.lo);
     }
 };
 // binary16 deviations times the storage scale (f - w_p, g itself), FP32
@@ -143,6 +150,9 @@ template <> struct Fmt3<P_FP16_DEV> {
     }
     static __device__ __forceinline__ S from_f(double f, int p, double s) {
         return __half_as_ushort(__float2half_rn((float)((f - plane_rest3<double>(p)) * s)));
+    }
+    static __device__ __forceinline__ S from_fd(double, double d, int, double s) {
+        return __half_as_ushort(__float2half_rn((float)(d * s)));
     }
 };
 
@@ -852,34 +862,66 @@ struct Fields7 {
     double* f[7];
 };
 
-// Equilibrium initialisation from seven FP64 device fields.
+// Equilibrium initialisation from seven FP64 device fields.  f^eq = w [r -
+// 3/2 r u^2 - 3/4 B^2 + 3 r c.u + 9/2 r (c.u)^2 + 9/4 B^2 |c|^2 - 9/2 (c.B)^2]
+// with the node terms formed once (the kernel is bound by the FP64 rate);
+// the deviation f^eq - w replaces r by r - 1, so the deviation formats take
+// it without cancellation.  g_q^eq = (1/6) [B + 3 ((C_q.u) B - (C_q.B) u)]:
+// the component along the axis is B_a / 6, the others carry +-3 E_ab with
+// E_ab = u_a B_b - B_a u_b.
 template <int P>
 __global__ void init3_kernel(Fields7 in, long long n, typename Fmt3<P>::S* __restrict__ st,
                              long long ps, double s16) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double rho = in.f[0][i], u[3] = {in.f[1][i], in.f[2][i], in.f[3][i]},
+        const double r = in.f[0][i], u[3] = {in.f[1][i], in.f[2][i], in.f[3][i]},
                      B[3] = {in.f[4][i], in.f[5][i], in.f[6][i]};
         const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
         const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const double r3 = 3.0 * r, r45 = 4.5 * r, m225 = 2.25 * bb;
+        const double common = -1.5 * r * uu - 0.75 * bb;
+        const double a_abs = r + common, a_dev = (r - 1.0) + common;
 #pragma unroll
         for (int p = 0; p < kQ; ++p) {
             const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
-            const double cu = cx * u[0] + cy * u[1] + cz * u[2];
-            const double cb = cx * B[0] + cy * B[1] + cz * B[2];
+            double cu = 0.0, cb = 0.0;
+            if (cx) {
+                cu += cx > 0 ? u[0] : -u[0];
+                cb += cx > 0 ? B[0] : -B[0];
+            }
+            if (cy) {
+                cu += cy > 0 ? u[1] : -u[1];
+                cb += cy > 0 ? B[1] : -B[1];
+            }
+            if (cz) {
+                cu += cz > 0 ? u[2] : -u[2];
+                cb += cz > 0 ? B[2] : -B[2];
+            }
+            const int cc = cx * cx + cy * cy + cz * cz;
+            double t = r3 * cu + r45 * cu * cu - 4.5 * cb * cb;
+            if (cc) t += m225 * cc;
             const double w = wq<double>(p);
-            const double f = w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) +
-                             4.5 * w * (0.5 * bb * (cx * cx + cy * cy + cz * cz) - cb * cb - bb / 6.0);
-            st[p * ps + i] = Fmt3<P>::from_f(f, p, s16);
+            st[p * ps + i] = Fmt3<P>::from_fd(w * (a_abs + t), w * (a_dev + t), p, s16);
         }
+        const double E3[3] = {3.0 * (u[1] * B[2] - B[1] * u[2]), 3.0 * (u[0] * B[2] - B[0] * u[2]),
+                              3.0 * (u[0] * B[1] - B[0] * u[1])};  // 3 E_yz, 3 E_xz, 3 E_xy
+        const double sixth = 1.0 / 6.0;
 #pragma unroll
         for (int q = 0; q < kM; ++q) {
             const int a = q / 2;
             const double sg = q % 2 ? -1.0 : 1.0;
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
-                st[(kQ + 3 * q + b) * ps + i] = Fmt3<P>::from_f(
-                    (B[b] + 3.0 * sg * (u[a] * B[b] - B[a] * u[b])) / 6.0, kQ + 3 * q + b, s16);
+            for (int b = 0; b < 3; ++b) {
+                double gv;
+                if (b == a) {
+                    gv = sixth * B[b];
+                } else {
+                    // E_ab = -E_ba; E3 is indexed by the axis not in {a, b}
+                    const double e = (a < b ? 1.0 : -1.0) * E3[3 - a - b];
+                    gv = sixth * (B[b] + sg * e);
+                }
+                st[(kQ + 3 * q + b) * ps + i] = Fmt3<P>::from_fd(gv, gv, kQ + 3 * q + b, s16);
+            }
         }
     }
 }
