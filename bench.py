@@ -702,9 +702,12 @@ def run_ours(args):
                 "hbm_frac": b3 * n3 ** 3 * s3 / t / 1e9 / hbm,
                 "note": "3D decaying turbulence (band 2 <= |n| <= 4, rms 0.04), local LES rates"}
         # the gradient closures, fraction at the one-pass bound of 360 B/node:
-        # the fused kernel (default), and the two-pass kernels (a moments pass
-        # reading 45 planes and writing 7, then the step: 596 B/node)
+        # the warp-specialised kernel (default), the fused kernel with two
+        # barriers per plane, and the two-pass kernels (a moments pass reading
+        # 45 planes and writing 7, then the step: 596 B/node)
+        kernel_names = {0: "fused", 1: "two-pass", 2: "two-pass", 3: "warp-specialised"}
         for name, les, launch in (("fp32_kinetic_les", 2, None), ("fp32_cross_helicity", 3, None),
+                                  ("fp32_kinetic_les_fused", 2, (0, 4)),
                                   ("fp32_kinetic_les_two_pass", 2, (2, 128))):
             n3 = args.n3
             h3 = L.lbmhd3_create(n3, n3, n3, L.lbmhd_params_default(
@@ -712,6 +715,7 @@ def run_ours(args):
                 stream=stream))
             if launch:
                 L.lbmhd3_set_launch(h3, *launch)
+            kname = kernel_names[L.lbmhd3_get_launch(h3)[0]]
             L.lbmhd3_init(h3, *inputs.turbulence3d(n3, n3, n3, seed=1 + rank))
             barrier()
             s3, t = timed_leg(L, h3, stream, 3, max_over_ranks_, step=L.lbmhd3_step)
@@ -721,10 +725,10 @@ def run_ours(args):
                 "MLUPS": world * n3 ** 3 * s3 / t / 1e6, "steps": s3, "seconds": t,
                 "lattice": f"{n3}^3", "bytes_per_cell": b3,
                 "hbm_frac": b3 * n3 ** 3 * s3 / t / 1e9 / hbm,
-                "kernel": "two-pass" if launch else "fused",
+                "kernel": kname,
                 "note": ("the paper's filtered equilibria" if les == 2 else
-                         "cross-helicity closure") + (", moments pass + step" if launch else
-                                                      ", one launch per step")}
+                         "cross-helicity closure") + (", moments pass + step" if kname == "two-pass"
+                                                      else ", one launch per step")}
 
     # ---- the FP64 diagnostics reduction on the same lattice ----------------
     # algorithmic bytes: the 19 stored planes, read once (the tiles' halo

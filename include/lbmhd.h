@@ -447,7 +447,12 @@ int lbmhd3_diagnostics(lbmhd3_t* h, double* out12);
  * reported as 4): the fused one-pass kernel, in which a CTA sweeps a tile of
  * 32 x 4 columns along z keeping the fields of consecutive planes and the
  * tile's pulled values in shared memory; the default for FP32 closures.
- * Results do not depend on it. */
+ * vec 3 (les 2, 3 in FP32 or FP16 storage; block 8 = tile rows): the
+ * warp-specialised one-pass kernel, in which producer warps pull the planes
+ * ahead of the consumer warps that collide them, handing shared-memory
+ * slots over on mbarriers with bounded waits; an expired wait makes the
+ * next synchronising call return LBMHD_ETIMEOUT.  EINVAL for a shape the
+ * handle's closure or format does not take.  Results do not depend on it. */
 int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block);
 int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
 int lbmhd3_sync(lbmhd3_t* h);

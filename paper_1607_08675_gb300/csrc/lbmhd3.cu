@@ -34,6 +34,7 @@
 #include <string>
 #include <type_traits>
 
+#include "lbmhd_bulk.cuh"
 #include "lbmhd_device.cuh"
 #include "lbmhd_internal.h"
 #include "lbmhd_step_body.cuh"
@@ -823,6 +824,204 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 || P == P_FF ? 1 : 3)
     }
 }
 
+// ---- warp-specialised fused form -------------------------------------------
+// The same fields, differences and collision as fused3_kernel (and the
+// two-pass kernels), so the same bits, with the pulls of the neighbourhood
+// taken off the collision's critical path.  A CTA of 640 threads owns a tile
+// of 32 x 8 columns.  Warps 8-19 are producers: one of the 34 x 10 tile and
+// halo nodes per thread, they pull its 45 populations of plane z and write
+// its seven fields into a ring of kWF plane slots in shared memory.  Warps
+// 0-7 are consumers (warp = tile row, lane = column): for plane z each pulls
+// its own node's 45 populations again (lines the producers pulled two
+// planes earlier, from L2), issuing the loads before it waits for the
+// fields of plane z + 1, then takes the central differences from the ring,
+// collides and stores.  Keeping the pulled values of the tile in shared
+// memory instead (a 138 KB ring) measured slower: shared memory takes L1's
+// room, and L1 holds the loads in flight.  The register file is split by
+// warpgroup (setmaxnreg): producers hold their pulled values in 64
+// registers, consumers theirs and the collision in 144 (384 x 64 + 256 x 144
+// = 640 x 96, the launch's registers, confirmed on the host from the
+// compiled kernel before the first launch).  Producers and consumers hand
+// slots over on shared-memory mbarriers, one arrival per warp after a warp
+// barrier: full[K mod kWB] completes when every producer warp has written
+// the fields of plane index K (each arrival a release, the waits acquire),
+// empty[K mod kWF] when every consumer warp is done reading slot K.  With
+// four slots the producers pull plane z + 3 while the consumers collide
+// plane z (deeper rings measured slower).  A CTA is persistent over work
+// units (tile, z-segment): unit u = blockIdx.x + i gridDim.x, each segment
+// pulling one plane below and one above its own, and the counters run on
+// across units, so a unit's first pulls overlap the previous unit's last
+// collisions.  Every wait is bounded (~2 s); on expiry the warp sets bit 1
+// of *status, and every warp leaves at its next check.
+constexpr int kWX = 32, kWY = 8, kWF = 4, kWB = 4;
+constexpr int kWsCons = kWX * kWY, kWsProd = 384, kWsThreads = kWsCons + kWsProd;
+constexpr int kWsLaunchRegs = 96, kWsProdRegs = 64, kWsConsRegs = 144;
+static_assert(kWsProd * kWsProdRegs + kWsCons * kWsConsRegs <= kWsThreads * kWsLaunchRegs,
+              "the warpgroups' registers exceed the launch's");
+static_assert(kWsThreads * kWsLaunchRegs <= 65536, "the launch's registers exceed an SM's");
+constexpr int kWsHX = kWX + 2, kWsHP = kWsHX * (kWY + 2);  // halo row, halo plane (340)
+static_assert(kWsHP <= kWsProd, "one tile or halo node per producer thread");
+// phases: a consumer's wait for plane index K must not see the phase of
+// K + kWB (the producers can run at most kWF - 2 planes past it)
+static_assert(kWB >= kWF - 2 && kWB >= 3, "full-barrier ring too short for the slot ring");
+constexpr size_t kWsSmem = (size_t)kWF * 7 * kWsHP * 4 + (kWB + kWF) * 8 + 16;
+
+// The 45 populations streamed into node (x, y, z), stored values.
+template <int P>
+__device__ __forceinline__ void pull_raw3(const typename Fmt3<P>::S* __restrict__ src, const Geom3& g,
+                                          int x, int y, int z, typename Fmt3<P>::S (&raw)[kP]) {
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+        const int cx = pcx(p), cy = pcy(p), cz = pcz(p);
+        const int rx = cx == 0 ? x : (cx > 0 ? xm : xp);
+        const int ry = cy == 0 ? y : (cy > 0 ? ym : yp);
+        const int rz = cz == 0 ? z : (cz > 0 ? zm : zp);
+        const unsigned off = ((unsigned)rz * (unsigned)g.ny + (unsigned)ry) * (unsigned)g.nx + (unsigned)rx;
+        raw[p] = __ldg(src + p * g.ps + off);
+    }
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    ws3_kernel(const typename Fmt3<P>::S* __restrict__ src, typename Fmt3<P>::S* __restrict__ dst,
+               Geom3 g, int tiles_x, int tiles_y, int seglen, int units,
+               Coll3<typename Fmt3<P>::R> c, int* status) {
+    using R = typename Fmt3<P>::R;
+    using S = typename Fmt3<P>::S;
+    static_assert(std::is_same<R, float>::value, "the warp-specialised kernel is for FP32 arithmetic");
+    extern __shared__ __align__(16) unsigned char ws3_smem[];
+    R* fring = reinterpret_cast<R*>(ws3_smem);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(fring + kWF * 7 * kWsHP);
+    unsigned long long* empty = full + kWB;
+    int* abort_ = reinterpret_cast<int*>(empty + kWF);
+    const int tid = threadIdx.x, lane = tid & 31;
+    constexpr unsigned kAll = 0xffffffffu;
+    if (tid == 0) {
+        for (int b = 0; b < kWB; ++b) mbar_init(&full[b], kWsProd / 32);
+        for (int b = 0; b < kWF; ++b) mbar_init(&empty[b], kWsCons / 32);
+        *abort_ = 0;
+    }
+    __syncthreads();
+    const int tiles = tiles_x * tiles_y;
+    // Control flow stays warp-uniform: each lane waits (its own acquire), and
+    // the warp goes on only if every lane's wait completed.
+    auto wait_all = [&](unsigned long long* bar, unsigned parity) {
+        const bool ok = __all_sync(kAll, mbar_wait_bounded(bar, parity));
+        if (!ok && lane == 0) {
+            atomicExch(abort_, 1);
+            atomicOr(status, 2);
+        }
+        return ok;
+    };
+    auto stop = [&]() { return __any_sync(kAll, *(volatile int*)abort_ != 0); };
+    auto failed = [&]() { return __any_sync(kAll, (*(volatile int*)status & 2) != 0); };
+
+    if (tid < kWsCons) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kWsConsRegs));
+        // ---- consumers: plane z0 + j of a unit reads the field slots of
+        // producer indices Kb + j, + 1, + 2 (planes z - 1, z, z + 1)
+        const int ly = tid >> 5, lx = lane;
+        unsigned Kb = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+            if (failed()) return;
+            const int tile = u % tiles, seg = u / tiles;
+            const int x0 = (tile % tiles_x) * kWX, y0 = (tile / tiles_x) * kWY;
+            const int tw = min(kWX, g.nx - x0), th = min(kWY, g.ny - y0);
+            const int z0 = g.zb + seg * seglen, n = min(z0 + seglen, g.ze) - z0;
+            const bool live = lx < tw && ly < th;
+            const int x = live ? x0 + lx : 0, y = live ? y0 + ly : 0;
+            const int c0 = (ly + 1) * kWsHX + lx + 1;
+            for (int j = 0; j < n; ++j) {
+                if (stop()) return;
+                const unsigned Kf = Kb + (unsigned)j + 2;
+                S raw[kP];
+                if (live) pull_raw3<P>(src, g, x, y, z0 + j, raw);
+                if (!wait_all(&full[Kf % kWB], (Kf / kWB) & 1)) return;
+                R d[kQ], gg[3 * kM];
+                if (live) {
+                    const R* sm = fring + (size_t)((Kb + j) % kWF) * 7 * kWsHP;
+                    const R* s0 = fring + (size_t)((Kb + j + 1) % kWF) * 7 * kWsHP;
+                    const R* sp = fring + (size_t)(Kf % kWF) * 7 * kWsHP;
+#pragma unroll
+                    for (int p = 0; p < kQ; ++p) d[p] = Fmt3<P>::dec(raw[p], p, c.i16);
+#pragma unroll
+                    for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q], kQ + q, c.i16);
+                    closure_collide3<R, MODE>(d, gg, c, [&](int q, int nb) {
+                        const int o = q * kWsHP;
+                        return nb == 0 ? s0[o + c0 + 1]
+                             : nb == 1 ? s0[o + c0 - 1]
+                             : nb == 2 ? s0[o + c0 + kWsHX]
+                             : nb == 3 ? s0[o + c0 - kWsHX]
+                             : nb == 4 ? sp[o + c0]
+                                       : sm[o + c0];
+                    });
+                }
+                // slot Kb + j (plane z - 1) is read for the last time: hand it
+                // back (after a warp barrier) before the stores
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(Kb + j) % kWF]);
+                if (live) {
+                    const unsigned row = ((unsigned)z0 + (unsigned)j) * (unsigned)g.ny + (unsigned)y;
+                    const unsigned o = row * (unsigned)g.nx + (unsigned)x;
+#pragma unroll
+                    for (int i = 0; i < kQ; ++i) dst[i * g.ps + o] = Fmt3<P>::enc(d[i], i, c.s16);
+#pragma unroll
+                    for (int q = 0; q < 3 * kM; ++q)
+                        dst[(kQ + q) * g.ps + o] = Fmt3<P>::enc(gg[q], kQ + q, c.s16);
+                }
+            }
+            // the unit's last two slots (its top plane and the one above)
+            if (lane == 0) {
+                mbar_arrive(&empty[(Kb + n) % kWF]);
+                mbar_arrive(&empty[(Kb + n + 1) % kWF]);
+            }
+            Kb += (unsigned)n + 2;
+        }
+        return;
+    }
+
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kWsProdRegs));
+    // ---- producers: plane index K (unit-local k = 0 .. n + 1, plane
+    // z0 - 1 + k) into slot K mod kWF, once the consumers have handed back
+    // slot K - kWF
+    const int pt = tid - kWsCons;
+    unsigned K = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        if (failed()) return;
+        const int tile = u % tiles, seg = u / tiles;
+        const int x0 = (tile % tiles_x) * kWX, y0 = (tile / tiles_x) * kWY;
+        const int tw = min(kWX, g.nx - x0), th = min(kWY, g.ny - y0);
+        const int z0 = g.zb + seg * seglen, n = min(z0 + seglen, g.ze) - z0;
+        const int hw = tw + 2;
+        const bool mine = pt < hw * (th + 2);
+        const int hy = mine ? pt / hw : 0, hx = mine ? pt - hy * hw : 0;
+        const int x = wrap3i(x0 - 1 + hx, g.nx), y = wrap3i(y0 - 1 + hy, g.ny);
+        const int hi = hy * kWsHX + hx;
+        for (int k = 0; k <= n + 1; ++k, ++K) {
+            if (stop()) return;
+            if (K >= kWF && !wait_all(&empty[K % kWF], ((K / kWF) - 1) & 1)) return;
+            if (mine) {
+                S raw[kP];
+                pull_raw3<P>(src, g, x, y, wrap3i(z0 - 1 + k, g.nz), raw);
+                R d[kQ], gg[3 * kM], m[7];
+#pragma unroll
+                for (int p = 0; p < kQ; ++p) d[p] = Fmt3<P>::dec(raw[p], p, c.i16);
+#pragma unroll
+                for (int q = 0; q < 3 * kM; ++q) gg[q] = Fmt3<P>::dec(raw[kQ + q], kQ + q, c.i16);
+                fields3<R>(d, gg, m);
+                R* slot = fring + (size_t)(K % kWF) * 7 * kWsHP;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) slot[q * kWsHP + hi] = m[q];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[K % kWB]);
+        }
+    }
+}
+
 template <int P, int V, int MODE>
 __global__ void __launch_bounds__(256) step3_kernel(const typename Fmt3<P>::S* __restrict__ src,
                                                     typename Fmt3<P>::S* __restrict__ dst,
@@ -1153,6 +1352,71 @@ cudaError_t launch_fused3_p(int les, const void* src, void* dst, const Geom3& g,
                     : launch_fused3<P, K3_CARATI>(src, dst, g, c, resident, st);
 }
 
+// The warp-specialised form: a persistent grid of at most `resident` CTAs
+// over tiles x segments work units.  The segment length balances the
+// units over the CTAs against the two extra planes each segment pulls.
+template <int P, int MODE>
+cudaError_t launch_ws3(const void* src, void* dst, const Geom3& g, const Coll3<float>& c,
+                       int resident, int* status, cudaStream_t st) {
+    using S = typename Fmt3<P>::S;
+    const int tiles_x = (g.nx + kWX - 1) / kWX, tiles_y = (g.ny + kWY - 1) / kWY;
+    const long long tiles = (long long)tiles_x * tiles_y;
+    const int nzr = g.ze - g.zb;
+    int best_seg = nzr;
+    double best = -1.0;
+    for (int seglen = nzr; seglen >= 1; seglen = seglen > 8 ? seglen - (seglen + 7) / 8 : seglen - 1) {
+        const long long units = tiles * ((nzr + seglen - 1) / seglen);
+        const long long per_cta = (units + resident - 1) / resident;
+        // planes computed over the busiest CTA's planes pulled
+        const double eff = (double)tiles * nzr / ((double)per_cta * resident * (seglen + 1.0));
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_seg = seglen;
+        }
+        if (units > 64LL * resident) break;
+    }
+    const long long units = tiles * ((nzr + best_seg - 1) / best_seg);
+    if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const int grid = (int)std::min<long long>(units, resident);
+    ws3_kernel<P, MODE><<<grid, kWsThreads, kWsSmem, st>>>((const S*)src, (S*)dst, g, tiles_x, tiles_y,
+                                                           best_seg, (int)units, c, status);
+    return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the warp-specialised kernel (FP32 and FP16
+// storage), 0 where it cannot run: its warpgroups' register split needs the
+// launch to hold kWsLaunchRegs registers per thread, which the compiled
+// kernel's register count must confirm.
+template <int P, int MODE>
+cudaError_t prepare_ws3_mode(int& per_sm) {
+    per_sm = 0;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, ws3_kernel<P, MODE>);
+    if (e != cudaSuccess || a.numRegs < kWsLaunchRegs) return e;
+    e = cudaFuncSetAttribute(ws3_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ws3_kernel<P, MODE>, kWsThreads, kWsSmem);
+    return e;
+}
+
+template <int P>
+cudaError_t prepare_ws3(int les, int& per_sm) {
+    if constexpr (P == P_FP32 || P == P_FP16_DEV)
+        return les == 2 ? prepare_ws3_mode<P, K3_FILTER>(per_sm) : prepare_ws3_mode<P, K3_CARATI>(per_sm);
+    per_sm = 0;
+    return cudaSuccess;
+}
+
+template <int P>
+cudaError_t launch_ws3_p(int les, const void* src, void* dst, const Geom3& g,
+                         const Coll3<typename Fmt3<P>::R>& c, int resident, int* status,
+                         cudaStream_t st) {
+    if constexpr (P == P_FP32 || P == P_FP16_DEV)
+        return les == 2 ? launch_ws3<P, K3_FILTER>(src, dst, g, c, resident, status, st)
+                        : launch_ws3<P, K3_CARATI>(src, dst, g, c, resident, status, st);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace d3
 }  // namespace lbmhd
 
@@ -1170,6 +1434,7 @@ struct lbmhd3_t {
     bool initialised, failed;
     int vec, block;      // vec 0: the fused closure kernel (block unused)
     int fused_resident;  // resident fused CTAs on the device
+    int ws_resident;     // resident warp-specialised CTAs on the device, 0 if unavailable
     int64_t steps, launches;
     void* mom;       // field planes of the gradient closures (les 2, 3)
     int* d_flag;     // bit 0: a non-finite value seen (check_finite_every)
@@ -1220,6 +1485,7 @@ int read_flag3(lbmhd3_t* h) {
     int flag = 0;
     LBMHD3_CK(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
+    if (flag & 2) return fail3(LBMHD_ETIMEOUT, "a bounded wait of the closure kernel expired");
     if (flag & 1) return fail3(LBMHD_ENONFINITE, "non-finite value detected in the 3D state");
     return LBMHD_OK;
 }
@@ -1257,10 +1523,12 @@ cudaError_t step3_planes(lbmhd3_t* h, int z0, int z1) {
         using R = typename Fmt3<P>::R;
         const Coll3<R> c = coll3<R>(h->p);
         if (h->vec == 0) return launch_fused3_p<P>(les, src, dst, g, c, h->fused_resident, h->stream);
+        if (h->vec == 3)
+            return launch_ws3_p<P>(les, src, dst, g, c, h->ws_resident, h->d_flag, h->stream);
         return h->vec == 2 ? launch3_pv<P, 2>(h->block, src, dst, g, c, les, h->mom, h->stream)
                            : launch3_pv<P, 1>(h->block, src, dst, g, c, les, h->mom, h->stream);
     });
-    if (e == cudaSuccess) h->launches += les >= 2 && h->vec != 0 ? 2 : 1;
+    if (e == cudaSuccess) h->launches += les >= 2 && (h->vec == 1 || h->vec == 2) ? 2 : 1;
     return e;
 }
 
@@ -1420,8 +1688,9 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
         }
     }
     // two nodes per thread where nx allows (8- or 16-byte loads), 128
-    // threads.  Gradient closures: FP32 takes the fused kernel, FP64 (bound
-    // by its FP64 arithmetic, where the fused kernel measured slower) the
+    // threads.  Gradient closures: FP32 and FP16 storage take the
+    // warp-specialised kernel (else the fused kernel), FP64 and FF (bound by
+    // their arithmetic, where the one-pass kernels measured slower) the
     // two-pass kernels one node per thread (two nodes need more than 255
     // registers in FP64).
     h->vec = nx % 2 == 0 && p->les < 2 && p->precision != LBMHD_FF ? 2 : 1;
@@ -1441,6 +1710,22 @@ int lbmhd3_create(int nx, int ny, int nz, const lbmhd_params* p, lbmhd3_t** out)
             return cuda3(nullptr, e, "fused closure kernel setup");
         }
         h->fused_resident = per_sm * nsm > 0 ? per_sm * nsm : 1;
+        h->ws_resident = 0;
+        if (p->precision == LBMHD_FP32 || p->precision == LBMHD_FP16_DEV) {
+            int ws_sm = 0;
+            e = by_prec3(p->precision, [&](auto tag) {
+                return prepare_ws3<decltype(tag)::value>(p->les, ws_sm);
+            });
+            if (e != cudaSuccess) {
+                lbmhd3_destroy(h);
+                return cuda3(nullptr, e, "warp-specialised closure kernel setup");
+            }
+            h->ws_resident = ws_sm * nsm;
+            if (h->ws_resident > 0) {
+                h->vec = 3;
+                h->block = kWY;
+            }
+        }
     }
     *out = h;
     return LBMHD_OK;
@@ -1453,6 +1738,16 @@ int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block) {
         if (h->p.les < 2) return fail3(LBMHD_EINVAL, "vec 0 (the fused kernel) is for les 2, 3");
         h->vec = 0;
         h->block = kFTY;
+        return LBMHD_OK;
+    }
+    if (vec == 3) {
+        if (h->p.les < 2 || (h->p.precision != LBMHD_FP32 && h->p.precision != LBMHD_FP16_DEV))
+            return fail3(LBMHD_EINVAL, "vec 3 (the warp-specialised kernel) is for les 2, 3 in FP32 or FP16 storage");
+        if (block != kWY) return fail3(LBMHD_EINVAL, "vec 3 takes block 8 (tile rows)");
+        if (h->ws_resident < 1)
+            return fail3(LBMHD_EINVAL, "the warp-specialised kernel cannot run on this device");
+        h->vec = 3;
+        h->block = block;
         return LBMHD_OK;
     }
     if ((vec != 1 && vec != 2) || h->geom.nx % vec)

@@ -31,6 +31,15 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
         : "memory");
 }
 
+// One arrival of the calling thread (release: its earlier shared-memory
+// writes are visible to a thread whose wait on the completed phase returns).
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(

@@ -200,12 +200,51 @@ def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
 
 
 @pytest.mark.parametrize("les", [2, 3])
+@pytest.mark.parametrize("shape", [(33, 17, 5), (70, 9, 3), (5, 3, 1), (1, 1, 1), (2, 2, 2),
+                                   (40, 40, 40), (96, 40, 48)])
+def test_warp_specialised_kernel_is_the_two_pass_kernel(L, les, shape):
+    """The warp-specialised kernel (vec 3, tiles of 32 x 8 columns) on ragged
+    tiles, one-node and size-2 axes, planes fewer than its rings, and a
+    lattice of many units (96 x 40 x 48: 15 tiles, segments of a few planes,
+    so each persistent CTA runs units one after another and its producer and
+    consumer counters wrap the rings across units): bit for bit the two-pass
+    kernel's result after 12 steps, in FP32 and FP16 storage."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + ny + nz)
+    fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
+        0.02 * rng.standard_normal((nz, ny, nx)) for _ in range(6))
+    for prec in ("fp32", "fp16_dev"):
+        kw = dict(KW, les=les, precision=prec)
+        ref = gpu3(L, fields, 12, 1, 128, **kw)[1]
+        got = gpu3(L, fields, 12, 3, 8, **kw)[1]
+        assert np.array_equal(got, ref), prec
+
+
+def test_warp_specialised_kernel_on_a_plane_range(L):
+    """Plane ranges (the z-slab step) through the warp-specialised kernel:
+    three ranges and a commit equal one whole step."""
+    fields = inputs.turbulence3d(64, 24, 20, seed=4)
+    kw = dict(KW, les=2, precision="fp32")
+    ref = gpu3(L, fields, 1, 1, 128, **kw)[1]
+    h = L.lbmhd3_create(64, 24, 20, L.lbmhd_params_default(**kw))
+    L.lbmhd3_set_launch(h, 3, 8)
+    L.lbmhd3_init(h, *fields)
+    for z0, z1 in ((0, 7), (7, 8), (8, 20)):
+        L.lbmhd3_step_planes(h, z0, z1)
+    L.lbmhd3_step_commit(h)
+    got = L.lbmhd3_get_state(h)
+    assert L.lbmhd3_launch_count(h) == 3
+    L.lbmhd3_destroy(h)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("les", [2, 3])
 def test_gradient_closure_launches_per_step(L, les):
     """Two launches per step in the two-pass form, one in the fused form."""
     fields = inputs.turbulence3d(8, 6, 4, seed=3)
-    for vec, per_step in ((1, 2), (0, 1)):
+    for vec, block, per_step in ((1, 128, 2), (0, 128, 1), (3, 8, 1)):
         h = L.lbmhd3_create(8, 6, 4, L.lbmhd_params_default(precision="fp32", les=les, **KW))
-        L.lbmhd3_set_launch(h, vec, 128)
+        L.lbmhd3_set_launch(h, vec, block)
         L.lbmhd3_init(h, *fields)
         L.lbmhd3_step(h, 5)
         assert L.lbmhd3_launch_count(h) == 5 * per_step and L.lbmhd3_step_count(h) == 5
@@ -261,10 +300,20 @@ def test_refused_configurations(L):
         L.lbmhd3_set_launch(h, 4, 128)
     with pytest.raises(L.LBMHDError):
         L.lbmhd3_set_launch(h, 0, 8)  # the fused kernel is for les 2, 3
+    with pytest.raises(L.LBMHDError):
+        L.lbmhd3_set_launch(h, 3, 8)  # and so is the warp-specialised one
     L.lbmhd3_destroy(h)
     h = L.lbmhd3_create(6, 4, 4, L.lbmhd_params_default(precision="fp32", les=2))
-    assert L.lbmhd3_get_launch(h) == (0, 4)  # FP32 closures default to the fused kernel
+    assert L.lbmhd3_get_launch(h) == (3, 8)  # FP32 closures: the warp-specialised kernel
+    for block in (2, 4, 16):
+        with pytest.raises(L.LBMHDError):
+            L.lbmhd3_set_launch(h, 3, block)  # 8 tile rows
     L.lbmhd3_destroy(h)
+    for prec in ("fp64", "ff"):  # FP32 arithmetic only
+        h = L.lbmhd3_create(6, 4, 4, L.lbmhd_params_default(precision=prec, les=3))
+        with pytest.raises(L.LBMHDError):
+            L.lbmhd3_set_launch(h, 3, 8)
+        L.lbmhd3_destroy(h)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16_dev", "ff"])

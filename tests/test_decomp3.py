@@ -209,14 +209,16 @@ def test_slabs3_on_one_gpu_match_monolithic(L, prec, les, k, nz, overlap):
 
 
 @pytest.mark.gpu
-def test_two_pass_slabs3_match_monolithic(L):
+@pytest.mark.parametrize("launch", [(2, 128), (0, 4)])
+def test_two_pass_slabs3_match_monolithic(L, launch):
     """The two-pass closure kernels (their moments pass around a plane
-    range) under slabs, against the fused kernel on the undivided lattice."""
+    range) and the barrier-per-plane fused kernel under slabs, against the
+    default (warp-specialised) kernel on the undivided lattice."""
     shape, steps = (32, 10, 14), 12
     fields = inputs.turbulence3d(*shape, kmin=1, kmax=3, rms=0.05, seed=9)
     for les in (2, 3):
         kw = dict(precision="fp32", tau_nu=0.6, tau_eta=0.65, C_S=0.2, delta=2.0, les=les)
-        sl = decomp.SlabRunner3(*shape, 3, launch=(2, 128), **kw)
+        sl = decomp.SlabRunner3(*shape, 3, launch=launch, **kw)
         sl.init(*fields)
         sl.step(steps)
         got = sl.state()
