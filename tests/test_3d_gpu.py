@@ -201,14 +201,16 @@ def test_fused_closure_kernel_is_the_two_pass_kernel(L, les, shape):
 
 @pytest.mark.parametrize("les", [2, 3])
 @pytest.mark.parametrize("shape", [(33, 17, 5), (70, 9, 3), (5, 3, 1), (1, 1, 1), (2, 2, 2),
-                                   (40, 40, 40), (96, 40, 48)])
+                                   (40, 40, 40), (96, 40, 48), (4, 3, 2), (36, 11, 7), (8, 1, 1),
+                                   (12, 5, 3)])
 def test_warp_specialised_kernel_is_the_two_pass_kernel(L, les, shape):
     """The warp-specialised kernel (vec 3, tiles of 32 x 8 columns) on ragged
     tiles, one-node and size-2 axes, planes fewer than its rings, and a
     lattice of many units (96 x 40 x 48: 15 tiles, segments of a few planes,
     so each persistent CTA runs units one after another and its producer and
     consumer counters wrap the rings across units): bit for bit the two-pass
-    kernel's result after 12 steps, in FP32 and FP16 storage."""
+    kernel's result after 12 steps, in FP32 and FP16 storage (4 x 3 x 2: one
+    tile wrapping on both sides; 36 x 11 x 7: a last tile of 4 columns)."""
     nx, ny, nz = shape
     rng = np.random.default_rng(nx + ny + nz)
     fields = (1 + 0.01 * rng.random((nz, ny, nx)),) + tuple(
