@@ -847,7 +847,8 @@ __global__ void __launch_bounds__(kFThreads, P == P_FP64 || P == P_FF ? 1 : 3)
 // the fields of plane index K (each arrival a release, the waits acquire),
 // empty[K mod kWF] when every consumer warp is done reading slot K.  With
 // four slots the producers pull plane z + 3 while the consumers collide
-// plane z (deeper rings measured slower).  A CTA is persistent over work
+// plane z (deeper rings measured slower); a producer issues its pulls before
+// it waits for its slot.  A CTA is persistent over work
 // units (tile, z-segment): unit u = blockIdx.x + i gridDim.x, each segment
 // pulling one plane below and one above its own, and the counters run on
 // across units, so a unit's first pulls overlap the previous unit's last
@@ -1002,10 +1003,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const int hi = hy * kWsHX + hx;
         for (int k = 0; k <= n + 1; ++k, ++K) {
             if (stop()) return;
+            // the pulls go out before the wait for the slot, which only
+            // guards the slot's writes
+            S raw[kP];
+            if (mine) pull_raw3<P>(src, g, x, y, wrap3i(z0 - 1 + k, g.nz), raw);
             if (K >= kWF && !wait_all(&empty[K % kWF], ((K / kWF) - 1) & 1)) return;
             if (mine) {
-                S raw[kP];
-                pull_raw3<P>(src, g, x, y, wrap3i(z0 - 1 + k, g.nz), raw);
                 R d[kQ], gg[3 * kM], m[7];
 #pragma unroll
                 for (int p = 0; p < kQ; ++p) d[p] = Fmt3<P>::dec(raw[p], p, c.i16);
