@@ -456,6 +456,14 @@ int lbmhd3_diagnostics(lbmhd3_t* h, double* out12);
 int lbmhd3_set_launch(lbmhd3_t* h, int vec, int block);
 int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block);
 int lbmhd3_sync(lbmhd3_t* h);
+/* Fault injection for tests of failure detection (the paper has no
+ * counterpart).  With LBMHD_DEBUG_DROP_BARRIER_ARRIVAL the producer warps
+ * of the warp-specialised closure kernel (vec 3) stop announcing their
+ * planes, so the consumer warps' bounded waits expire (~2 s), the kernel
+ * returns and the next synchronising call returns LBMHD_ETIMEOUT (the GPU
+ * context stays usable; lbmhd3_init or a state write clears the report).
+ * 0 clears it.  EINVAL for a NULL handle. */
+int lbmhd3_debug(lbmhd3_t* h, int flags);
 int64_t lbmhd3_step_count(const lbmhd3_t* h);
 int64_t lbmhd3_launch_count(const lbmhd3_t* h);
 

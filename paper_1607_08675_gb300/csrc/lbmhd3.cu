@@ -889,7 +889,7 @@ template <int P, int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1)
     ws3_kernel(const typename Fmt3<P>::S* __restrict__ src, typename Fmt3<P>::S* __restrict__ dst,
                Geom3 g, int tiles_x, int tiles_y, int seglen, int units,
-               Coll3<typename Fmt3<P>::R> c, int* status) {
+               Coll3<typename Fmt3<P>::R> c, int* status, int debug) {
     using R = typename Fmt3<P>::R;
     using S = typename Fmt3<P>::S;
     static_assert(std::is_same<R, float>::value, "the warp-specialised kernel is for FP32 arithmetic");
@@ -1020,7 +1020,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 for (int q = 0; q < 7; ++q) slot[q * kWsHP + hi] = m[q];
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full[K % kWB]);
+            // (fault injection: announcements dropped, the consumers' waits expire)
+            if (lane == 0 && !(debug & LBMHD_DEBUG_DROP_BARRIER_ARRIVAL)) mbar_arrive(&full[K % kWB]);
         }
     }
 }
@@ -1360,7 +1361,7 @@ cudaError_t launch_fused3_p(int les, const void* src, void* dst, const Geom3& g,
 // units over the CTAs against the two extra planes each segment pulls.
 template <int P, int MODE>
 cudaError_t launch_ws3(const void* src, void* dst, const Geom3& g, const Coll3<float>& c,
-                       int resident, int* status, cudaStream_t st) {
+                       int resident, int* status, int debug, cudaStream_t st) {
     using S = typename Fmt3<P>::S;
     const int tiles_x = (g.nx + kWX - 1) / kWX, tiles_y = (g.ny + kWY - 1) / kWY;
     const long long tiles = (long long)tiles_x * tiles_y;
@@ -1382,7 +1383,7 @@ cudaError_t launch_ws3(const void* src, void* dst, const Geom3& g, const Coll3<f
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(units, resident);
     ws3_kernel<P, MODE><<<grid, kWsThreads, kWsSmem, st>>>((const S*)src, (S*)dst, g, tiles_x, tiles_y,
-                                                           best_seg, (int)units, c, status);
+                                                           best_seg, (int)units, c, status, debug);
     return cudaGetLastError();
 }
 
@@ -1412,11 +1413,11 @@ cudaError_t prepare_ws3(int les, int& per_sm) {
 
 template <int P>
 cudaError_t launch_ws3_p(int les, const void* src, void* dst, const Geom3& g,
-                         const Coll3<typename Fmt3<P>::R>& c, int resident, int* status,
+                         const Coll3<typename Fmt3<P>::R>& c, int resident, int* status, int debug,
                          cudaStream_t st) {
     if constexpr (P == P_FP32 || P == P_FP16_DEV)
-        return les == 2 ? launch_ws3<P, K3_FILTER>(src, dst, g, c, resident, status, st)
-                        : launch_ws3<P, K3_CARATI>(src, dst, g, c, resident, status, st);
+        return les == 2 ? launch_ws3<P, K3_FILTER>(src, dst, g, c, resident, status, debug, st)
+                        : launch_ws3<P, K3_CARATI>(src, dst, g, c, resident, status, debug, st);
     return cudaErrorInvalidValue;
 }
 
@@ -1438,6 +1439,7 @@ struct lbmhd3_t {
     int vec, block;      // vec 0: the fused closure kernel (block unused)
     int fused_resident;  // resident fused CTAs on the device
     int ws_resident;     // resident warp-specialised CTAs on the device, 0 if unavailable
+    int debug;           // fault-injection flags (lbmhd3_debug)
     int64_t steps, launches;
     void* mom;       // field planes of the gradient closures (les 2, 3)
     int* d_flag;     // bit 0: a non-finite value seen (check_finite_every)
@@ -1527,7 +1529,7 @@ cudaError_t step3_planes(lbmhd3_t* h, int z0, int z1) {
         const Coll3<R> c = coll3<R>(h->p);
         if (h->vec == 0) return launch_fused3_p<P>(les, src, dst, g, c, h->fused_resident, h->stream);
         if (h->vec == 3)
-            return launch_ws3_p<P>(les, src, dst, g, c, h->ws_resident, h->d_flag, h->stream);
+            return launch_ws3_p<P>(les, src, dst, g, c, h->ws_resident, h->d_flag, h->debug, h->stream);
         return h->vec == 2 ? launch3_pv<P, 2>(h->block, src, dst, g, c, les, h->mom, h->stream)
                            : launch3_pv<P, 1>(h->block, src, dst, g, c, les, h->mom, h->stream);
     });
@@ -2017,6 +2019,12 @@ int lbmhd3_sync(lbmhd3_t* h) {
     if (rc) return rc;
     LBMHD3_CK(h, cudaStreamSynchronize(h->stream));
     return h->initialised ? read_flag3(h) : LBMHD_OK;
+}
+
+int lbmhd3_debug(lbmhd3_t* h, int flags) {
+    if (!h) return fail3(LBMHD_EINVAL, "handle is NULL");
+    h->debug = flags;
+    return LBMHD_OK;
 }
 
 int64_t lbmhd3_step_count(const lbmhd3_t* h) { return h ? h->steps : 0; }

@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
                 "lbmhd3_set_launch": (i, [h, i, i]),
                 "lbmhd3_get_launch": (i, [h, ctypes.POINTER(i), ctypes.POINTER(i)]),
                 "lbmhd3_sync": (i, [h]),
+                "lbmhd3_debug": (i, [h, i]),
                 "lbmhd3_step_count": (ctypes.c_int64, [h]),
                 "lbmhd3_launch_count": (ctypes.c_int64, [h]),
                 "lbmhd3_bytes_per_cell": (i, [i]),
@@ -453,6 +454,10 @@ def lbmhd3_get_launch(h: Handle3):
 
 def lbmhd3_sync(h: Handle3):
     _check(lib().lbmhd3_sync(h.ptr))
+
+
+def lbmhd3_debug(h: Handle3, flags: int):
+    _check(lib().lbmhd3_debug(h.ptr, int(flags)))
 
 
 def lbmhd3_step_count(h: Handle3) -> int:

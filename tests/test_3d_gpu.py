@@ -222,6 +222,30 @@ def test_warp_specialised_kernel_is_the_two_pass_kernel(L, les, shape):
         assert np.array_equal(got, ref), prec
 
 
+def test_warp_specialised_kernel_timeout_is_reported_not_hung(L):
+    """Host-requested fault: the producer warps stop announcing their planes,
+    so the consumers' bounded waits expire; the step returns, the next
+    synchronising call reports ETIMEOUT, and after a fresh init the handle
+    steps correctly again."""
+    fields = inputs.turbulence3d(64, 24, 20, seed=5)
+    kw = dict(KW, les=2, precision="fp32")
+    ref = gpu3(L, fields, 3, 1, 128, **kw)[1]
+    h = L.lbmhd3_create(64, 24, 20, L.lbmhd_params_default(**kw))
+    assert L.lbmhd3_get_launch(h) == (3, 8)
+    L.lbmhd3_init(h, *fields)
+    L.lbmhd3_debug(h, L.DEBUG_DROP_BARRIER_ARRIVAL)
+    L.lbmhd3_step(h, 1)
+    with pytest.raises(L.LBMHDError) as e:
+        L.lbmhd3_sync(h)
+    assert e.value.code == -5
+    L.lbmhd3_debug(h, 0)
+    L.lbmhd3_init(h, *fields)
+    L.lbmhd3_step(h, 3)
+    got = L.lbmhd3_get_state(h)
+    L.lbmhd3_destroy(h)
+    assert np.array_equal(got, ref)
+
+
 def test_warp_specialised_kernel_on_a_plane_range(L):
     """Plane ranges (the z-slab step) through the warp-specialised kernel:
     three ranges and a commit equal one whole step."""
