@@ -862,9 +862,12 @@ static_assert(kWsProd * kWsProdRegs + kWsCons * kWsConsRegs <= kWsThreads * kWsL
 static_assert(kWsThreads * kWsLaunchRegs <= 65536, "the launch's registers exceed an SM's");
 constexpr int kWsHX = kWX + 2, kWsHP = kWsHX * (kWY + 2);  // halo row, halo plane (340)
 static_assert(kWsHP <= kWsProd, "one tile or halo node per producer thread");
-// phases: a consumer's wait for plane index K must not see the phase of
-// K + kWB (the producers can run at most kWF - 2 planes past it)
-static_assert(kWB >= kWF - 2 && kWB >= 3, "full-barrier ring too short for the slot ring");
+// A producer warp arriving for plane index K must find every producer warp
+// past K - kWB.  It has waited for slot K - kWF to be handed back, and the
+// consumers hand back a unit's last two slots after waiting only for its
+// last plane, so all producers are known to be past K - kWF, no further:
+// the barrier ring must be at least as long as the slot ring.
+static_assert(kWB >= kWF && kWB >= 3, "full-barrier ring shorter than the slot ring");
 constexpr size_t kWsSmem = (size_t)kWF * 7 * kWsHP * 4 + (kWB + kWF) * 8 + 16;
 
 // The 45 populations streamed into node (x, y, z), stored values.
