@@ -1776,6 +1776,7 @@ int lbmhd3_get_launch(const lbmhd3_t* h, int* vec, int* block) {
 
 int lbmhd3_init(lbmhd3_t* h, const double* rho, const double* ux, const double* uy,
                 const double* uz, const double* bx, const double* by, const double* bz) {
+    TraceRange trace_("lbmhd3_init");
     int rc = check3(h);
     if (rc) return rc;
     const double* f[7] = {rho, ux, uy, uz, bx, by, bz};
@@ -1882,6 +1883,7 @@ int lbmhd3_set_state_raw(lbmhd3_t* h, const void* state, size_t bytes) {
 }
 
 int lbmhd3_step(lbmhd3_t* h, int n) {
+    TraceRange trace_("lbmhd3_step");
     int rc = check3(h);
     if (rc) return rc;
     if (n < 0) return fail3(LBMHD_EINVAL, "n must be >= 0");
@@ -1904,6 +1906,7 @@ int lbmhd3_step(lbmhd3_t* h, int n) {
 }
 
 int lbmhd3_step_planes(lbmhd3_t* h, int z0, int z1) {
+    TraceRange trace_("lbmhd3_step_planes");
     int rc = check3(h);
     if (rc) return rc;
     if (!(0 <= z0 && z0 < z1 && z1 <= h->geom.nz))
@@ -1958,6 +1961,7 @@ int lbmhd3_unpack_plane(lbmhd3_t* h, int z, uint64_t mask, const void* buf, void
 }
 
 int lbmhd3_moments(lbmhd3_t* h, double* out7) {
+    TraceRange trace_("lbmhd3_moments");
     int rc = check3(h);
     if (rc) return rc;
     if (!out7) return fail3(LBMHD_EINVAL, "NULL output");
@@ -1994,6 +1998,7 @@ int lbmhd3_get_state(lbmhd3_t* h, double* out) {
 }
 
 int lbmhd3_diagnostics(lbmhd3_t* h, double* out12) {
+    TraceRange trace_("lbmhd3_diagnostics");
     int rc = check3(h);
     if (rc) return rc;
     if (!out12) return fail3(LBMHD_EINVAL, "NULL output");

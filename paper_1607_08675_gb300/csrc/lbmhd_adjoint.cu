@@ -497,6 +497,7 @@ extern "C" {
 
 int lbmhd_adjoint_record(lbmhd_t* h, const double* rho0, const double* ux0, const double* uy0,
                          const double* bx0, const double* by0, int nsteps, int every) {
+    TraceRange trace_("lbmhd_adjoint_record");
     if (!h) return afail(LBMHD_EINVAL, "handle is NULL");
     if (h->failed) return afail(LBMHD_ECUDA, "handle is unusable after a CUDA error");
     if (!rho0 || !ux0 || !uy0 || !bx0 || !by0) return afail(LBMHD_EINVAL, "NULL field");
@@ -545,6 +546,7 @@ int lbmhd_adjoint_backward(lbmhd_t* h, const double* g_rho, const double* g_ux,
                            const double* g_uy, const double* g_bx, const double* g_by,
                            double* dtheta, double* d_rho0, double* d_ux0, double* d_uy0,
                            double* d_bx0, double* d_by0) {
+    TraceRange trace_("lbmhd_adjoint_backward");
     if (!h) return afail(LBMHD_EINVAL, "handle is NULL");
     if (h->failed) return afail(LBMHD_ECUDA, "handle is unusable after a CUDA error");
     Tape* t = (Tape*)h->tape;

@@ -642,6 +642,7 @@ int lbmhd_batch_init(lbmhd_batch_t* b, int run, const double* rho, const double*
 }
 
 int lbmhd_batch_step(lbmhd_batch_t* b, int n) {
+    TraceRange trace_("lbmhd_batch_step");
     int rc = check_batch(b);
     if (rc) return rc;
     if (n < 0) return bfail(LBMHD_EINVAL, "n must be >= 0");

@@ -9,7 +9,19 @@
 
 #include "lbmhd.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lbmhd {
+
+// A named range on the calling thread for profilers (NVTX; a no-op unless a
+// tool is attached), held for the duration of an entry point.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
 
 constexpr int kNumPlanes = 19;  // 9 f_i, then g_k (x, y) for k = 0..4
 

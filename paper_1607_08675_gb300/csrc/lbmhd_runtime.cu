@@ -321,6 +321,7 @@ int lbmhd_get_launch(const lbmhd_t* h, int* vec, int* block) {
 
 int lbmhd_init_device(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                       const double* bx, const double* by) {
+    TraceRange trace_("lbmhd_init_device");
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho || !ux || !uy || !bx || !by) return fail(LBMHD_EINVAL, "NULL field");
@@ -352,6 +353,7 @@ static bool device_views(const double* const* host, const double** dev) {
 
 int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy,
                const double* bx, const double* by) {
+    TraceRange trace_("lbmhd_init");
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho || !ux || !uy || !bx || !by) return fail(LBMHD_EINVAL, "NULL field");
@@ -386,6 +388,7 @@ int lbmhd_init(lbmhd_t* h, const double* rho, const double* ux, const double* uy
 }
 
 int lbmhd_step(lbmhd_t* h, int n) {
+    TraceRange trace_("lbmhd_step");
     int rc = check_handle(h);
     if (rc) return rc;
     if (n < 0) return fail(LBMHD_EINVAL, "n must be >= 0");
@@ -443,6 +446,7 @@ int lbmhd_moments_device(lbmhd_t* h, double* rho, double* ux, double* uy, double
 }
 
 int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, double* by) {
+    TraceRange trace_("lbmhd_moments");
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho || !ux || !uy || !bx || !by) return fail(LBMHD_EINVAL, "NULL field");
@@ -472,6 +476,7 @@ int lbmhd_moments(lbmhd_t* h, double* rho, double* ux, double* uy, double* bx, d
 }
 
 int lbmhd_diagnostics(lbmhd_t* h, lbmhd_diag* out) {
+    TraceRange trace_("lbmhd_diagnostics");
     int rc = check_handle(h);
     if (rc) return rc;
     if (!out) return fail(LBMHD_EINVAL, "out is NULL");
@@ -594,6 +599,7 @@ int lbmhd_copy_rows(lbmhd_t* dst, int dst_row, lbmhd_t* src, int src_row, int nr
 }
 
 int lbmhd_step_rows(lbmhd_t* h, int y0, int y1) {
+    TraceRange trace_("lbmhd_step_rows");
     int rc = check_handle(h);
     if (rc) return rc;
     if (!h->initialised) return fail(LBMHD_ESTATE, "lbmhd_step_rows before lbmhd_init");
