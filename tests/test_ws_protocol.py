@@ -14,7 +14,11 @@ that parity has completed, i.e. the current phase's parity differs.
 The model checks that every read sees the plane it expects, that no phase
 of a barrier collects arrivals meant for two different planes, and that the
 schedule never deadlocks -- for the kernel's ring lengths (F = B = 4), and
-that the same checks catch a barrier ring shorter than the slot ring."""
+that the same checks catch a barrier ring shorter than the slot ring.  A
+second model follows the failure path: every wait gives up after a bounded
+number of polls, sets the CTA's abort flag and the status, and every warp
+checks the flag once per plane; with the producers' announcements dropped
+(the host-requested fault) every warp must still finish."""
 import random
 
 import pytest
@@ -129,3 +133,70 @@ def test_barrier_ring_shorter_than_slot_ring_is_caught():
             except AssertionError:
                 found += 1
     assert found > 0
+
+
+def producer_bounded(units, F, B, full, empty, ctl, drop, limit):
+    K = 0
+    for n in units:
+        for k in range(n + 2):
+            if ctl["abort"]:
+                return
+            if K >= F:
+                b, par, polls = empty[K % F], ((K // F) - 1) & 1, 0
+                while not b.passed(par):
+                    polls += 1
+                    if polls > limit:
+                        ctl["abort"] = ctl["status"] = True
+                        return
+                    yield "wait"
+            if not drop:
+                full[K % B].arrive(K)
+            K += 1
+            yield "arrive"
+
+
+def consumer_bounded(units, F, B, full, empty, ctl, limit):
+    Kb = 0
+    for n in units:
+        for j in range(n):
+            if ctl["abort"]:
+                return
+            Kf = Kb + j + 2
+            b, par, polls = full[Kf % B], (Kf // B) & 1, 0
+            while not b.passed(par):
+                polls += 1
+                if polls > limit:
+                    ctl["abort"] = ctl["status"] = True
+                    return
+                yield "wait"
+            empty[(Kb + j) % F].arrive(Kb + j)
+            yield "arrive"
+        empty[(Kb + n) % F].arrive(Kb + n)
+        empty[(Kb + n + 1) % F].arrive(Kb + n + 1)
+        Kb += n + 2
+
+
+@pytest.mark.parametrize("drop", [False, True])
+def test_bounded_waits_end_every_warp(drop):
+    """With every announcement made, the run ends with no abort; with them
+    dropped, the waits expire, the status is set, and every warp returns
+    (a bounded number of scheduling steps)."""
+    for units in UNITS:
+        for seed in range(20):
+            rng = random.Random(seed)
+            P, C, F, B = 3, 2, 4, 4
+            full = [Barrier(P) for _ in range(B)]
+            empty = [Barrier(C) for _ in range(F)]
+            ctl = {"abort": False, "status": False}
+            warps = [producer_bounded(units, F, B, full, empty, ctl, drop, 500) for _ in range(P)]
+            warps += [consumer_bounded(units, F, B, full, empty, ctl, 500) for _ in range(C)]
+            live, steps = list(range(len(warps))), 0
+            while live:
+                w = rng.choice(live)
+                try:
+                    next(warps[w])
+                except StopIteration:
+                    live.remove(w)
+                steps += 1
+                assert steps < 10 ** 6, "a warp never returned"
+            assert ctl["status"] == drop
