@@ -1,5 +1,6 @@
-// lbmhd_bulk.cuh -- bulk asynchronous copies (cp.async.bulk, global to
-// shared) completing on shared-memory mbarriers, and a bounded wait.
+// lbmhd_bulk.cuh -- shared-memory mbarriers (init, plain and
+// transaction-count arrivals, a bounded wait) and bulk asynchronous copies
+// (cp.async.bulk, global to shared) that complete on them.
 //
 // A copy moves a multiple of 16 bytes between 16-byte aligned addresses.
 // Every wait is bounded: after ~2 s (4e9 cycles) it gives up and returns
